@@ -1,0 +1,4 @@
+"""GB300-native posterior-sampling sweep of Bayesian deconvolution
+(arXiv 2411.00991).  ``bdecon`` is the ctypes binding of the C-ABI CUDA
+library; ``synth`` draws seeded synthetic inputs."""
+__all__ = ["bdecon", "synth"]
