@@ -1,0 +1,389 @@
+"""Benchmark of the posterior-sampling sweep (pixel-updates/s).
+
+Workload: the 512x512 sCMOS widefield frame (PSF sigma ~1.2 px on 17x17,
+offset/variance maps, gain 2.1, 1 chain), float sweep form.  One step = 50
+sweeps of every chain = one refresh period: the sweep kernel (propose,
+window likelihood change, patch prior change, accept/write, running mean)
+followed by the double-precision refresh of mu, spectra and log posterior
+and the trace assembly.  Inputs are resident in HBM; L2 is flushed (a 256 MB
+write) between timed steps because the working set (~10 MB) fits in L2.
+
+value     pixel-updates/s of the float form (object pixels x chains x sweeps / s)
+e2e       same metric through the C ABI from host buffers: create (H2D of frame
+          and maps, set-up, initial refresh), 50 sweeps, posterior mean (D2H)
+fp64      the plain double sampler on the same frame (extra key)
+roofline  sweep kernel, plain-ALU bound (see the design doc for the op count)
+cpu_baseline  the C oracle on a 128x128 crop of the same frame, 1 sweep per core
+
+--impl reference runs the oracle (the CPU restatement of the method) as the
+reference arm on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2411_00991_gb300 import synth  # noqa: E402
+
+METRIC = "pixel-updates/s, FP32 batched vs FP64 plain on one GB300; % of BW roofline"
+SWEEPS_PER_STEP = 50
+CROP = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
+                    source="measured")
+    except Exception:
+        return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.rows.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------- CPU baseline --
+def crop_problem(prob, side=CROP, y0=192, x0=192):
+    """A side x side region of the frame with its maps: a bounded sample of
+    the same workload (same PSF, camera model, structure density)."""
+    import copy
+    q = copy.copy(prob)
+    sl = (slice(y0, y0 + side), slice(x0, x0 + side))
+    q.image = np.ascontiguousarray(prob.image[sl])
+    q.offset = prob.offset if np.isscalar(prob.offset) else np.ascontiguousarray(prob.offset[sl])
+    q.var = prob.var if np.isscalar(prob.var) else np.ascontiguousarray(prob.var[sl])
+    q.gain = prob.gain if np.isscalar(prob.gain) else np.ascontiguousarray(prob.gain[sl])
+    q.truth = None
+    q.name = prob.name + f"_crop{side}"
+    return q
+
+
+def _oracle_job(args):
+    seed, sweeps = args
+    from oracle import oracle as O
+    prob = crop_problem(synth.widefield_512())
+    prob.seed = seed
+    orc = O.Oracle(prob)
+    t = time.perf_counter()
+    orc.run(sweeps)
+    dt = time.perf_counter() - t
+    Ho, Wo = prob.object_shape()
+    return Ho * Wo * sweeps, dt
+
+
+def cpu_baseline(sweeps=1, cores=None):
+    """The oracle as it stands, one independent chain per host core (spawned
+    processes), on the 128x128 crop; returns updates/s over the wall time."""
+    from oracle import oracle as O
+    O.build()
+    n = cores or min(os.cpu_count() or 1, 16)
+    ctx = mp.get_context("spawn")
+    t = time.perf_counter()
+    with ctx.Pool(n) as pool:
+        res = pool.map(_oracle_job, [(1000 + k, sweeps) for k in range(n)])
+    wall = time.perf_counter() - t
+    upd = sum(r[0] for r in res)
+    per_proc = float(np.mean([r[0] / r[1] for r in res]))
+    return dict(value=upd / wall, unit="pixel-updates/s", cores=n, kind="oracle",
+                sample=f"{CROP}x{CROP} crop of the 512x512 frame (L=17), {sweeps} sweep(s) per core, "
+                       f"one chain per core; wall {wall:.1f} s incl. process start",
+                per_core=per_proc)
+
+
+# ------------------------------------------------------------ op counting --
+def flops_per_update(prob, mu):
+    """Algorithmic float operations of one update (FMA = 2): for each window
+    pixel 6 per photon-count term (term, Gaussian factor, power and sum
+    recurrences) + 40 fixed (mode, logs, ratios), for each half-spectrum
+    entry of the patch 22.  The term count is the number of photon counts
+    carrying >= 2^-26 of the pixel's photon posterior at the current mu."""
+    g, o, v = prob.maps()
+    c = (prob.image.astype(np.float64) - o) / g
+    s2 = v / g ** 2
+    mu = np.maximum(mu, 1e-12)
+    phi = np.arange(0, int(max(c.max(), mu.max()) + 60))[:, None]
+    cf, s2f, muf = c.ravel()[None, :], s2.ravel()[None, :], mu.ravel()[None, :]
+    from scipy.special import gammaln
+    lt = -(cf - phi) ** 2 / (2 * s2f) + phi * np.log(muf) - gammaln(phi + 1)
+    lt -= lt.max(axis=0, keepdims=True)
+    w = np.exp(lt)
+    w /= w.sum(axis=0, keepdims=True)
+    nterms = float((w >= 2.0 ** -26).sum(axis=0).mean())
+    L = prob.L
+    nhalf = (prob.S * prob.S + 1) // 2
+    return L * L * (6 * nterms + 40) + nhalf * 22, nterms
+
+
+# ---------------------------------------------------------------- our arm --
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2411_00991_gb300 import bdecon
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    prob = synth.widefield_512()
+    prob.seed = prob.seed + 7919 * rank             # weak scaling: one independent chain per rank
+    W, K, S = args.warmup, args.steps, SWEEPS_PER_STEP
+    prob.burn_in = W * S                            # every timed sweep enters the running mean
+    prob.refresh_every = S
+    Ho, Wo = prob.object_shape()
+    upd_per_step = Ho * Wo * prob.n_chains * S
+    stream = torch.cuda.current_stream(dev)
+    total_sweeps = (W + K) * S + 8
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def l2_flush():
+        flush.fill_(1.0)
+
+    s = bdecon.Sampler(prob, precision=bdecon.BDECON_FP32, max_sweeps=total_sweeps,
+                       stream=stream.cuda_stream)
+    for _ in range(W):
+        s.sweep(S)
+    s.sync()
+    s.set_timing(True)
+    s.sweep_kernel_time()
+    n0 = s.launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            l2_flush()
+            evs[k][0].record(stream)
+            s.sweep(S)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    s.sync()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    launches = s.launch_count() - n0
+    kms, klaunch = s.sweep_kernel_time()
+    mu = s.get_mu()
+    tr = s.trace()
+    acc = s.accept_counts()
+    plan = s.get_plan()
+    s.close()
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * upd_per_step * K / (ms / 1e3)
+
+    # plain double sampler on the same frame (fewer sweeps: it is ~50x slower)
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        s64 = bdecon.Sampler(prob, precision=bdecon.BDECON_FP64, max_sweeps=4 * S, stream=stream.cuda_stream)
+        s64.sweep(2)
+        s64.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n64 = args.fp64_sweeps
+        l2_flush()
+        e0.record(stream)
+        s64.sweep(n64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s64.sync()
+        t64 = e0.elapsed_time(e1)
+        s64.close()
+        fp64 = dict(value=Ho * Wo * n64 / (t64 / 1e3), unit="pixel-updates/s", sweeps=n64,
+                    ms_per_sweep=t64 / n64)
+
+    # end to end through the C ABI from host buffers
+    e2e = None
+    if rank == 0:
+        ep = synth.widefield_512()
+        ep.burn_in = S // 2
+        ep.refresh_every = S
+        h2d = ep.image.nbytes + np.asarray(ep.offset).nbytes + np.asarray(ep.var).nbytes + ep.psf.nbytes
+        d2h = Ho * Wo * 8
+        ke = min(K, 3)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(ke):
+            se = bdecon.Sampler(ep, precision=bdecon.BDECON_FP32, max_sweeps=S + 4, stream=stream.cuda_stream)
+            se.sweep(S)
+            mean = se.posterior_mean()
+            se.close()
+        dt = (time.perf_counter() - t) / ke
+        assert np.isfinite(mean).all()
+        e2e = dict(value=upd_per_step / dt, unit="pixel-updates/s", h2d_bytes_per_step=int(h2d),
+                   d2h_bytes_per_step=int(d2h), ms_per_step=dt * 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks = _peaks()
+    fpu, nterms = flops_per_update(prob, mu)
+    launch_ms = kms / max(klaunch, 1)
+    upd_per_launch = Ho * Wo * prob.n_chains * S        # one launch covers one refresh period
+    ach_tflops = fpu * upd_per_launch / (launch_ms / 1e3) / 1e12
+    clocks = clk.summary()
+    peak_tflops = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    alg_bytes_per_update = 68.0
+    ach_gbs = alg_bytes_per_update * upd_per_launch / (launch_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "pixel-updates/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": ms / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded filament+blob object, Poisson photons, sCMOS maps)",
+        "config": {"workload": "widefield 512x512 frame, Gaussian PSF sigma 1.2 px on 17x17, sCMOS offset "
+                               "N(100,2) / variance Gamma(2,1) maps, gain 2.1, 1 chain, float sweeps with "
+                               "double refresh every 50 sweeps",
+                   "sweeps_per_step": S, "object_pixels": Ho * Wo, "chains_per_gpu": prob.n_chains,
+                   "l2": "flushed (256 MB write) between timed steps", "plan": plan},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "kernel": "k_sweep<float>", "achieved": ach_tflops,
+                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach_tflops / peak_tflops,
+                     "traffic": None, "flops_per_update": fpu, "mean_photon_terms": nterms,
+                     "launch_ms": launch_ms, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"},
+        "bw_roofline": {"achieved": ach_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach_gbs / peaks["hbm_gbs"], "bytes_per_update": alg_bytes_per_update,
+                        "peak_source": peaks["source"]},
+        "fp64": fp64,
+        "acceptance": float(acc[-K * S:].sum() / (K * S * Ho * Wo)),
+        "trace_last": float(tr[-1]),
+    }
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(sweeps=1)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    W, K = args.warmup, args.steps
+    vals = []
+    cores = None
+    for k in range(W + K):
+        r = cpu_baseline(sweeps=1)
+        cores = r["cores"]
+        if k >= W:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    side = CROP + 16
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": v,
+        "unit": "pixel-updates/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": side * side * cores / v * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic (seeded filament+blob object, Poisson photons, sCMOS maps)",
+        "config": {"workload": "widefield 512x512 frame, Gaussian PSF sigma 1.2 px on 17x17, sCMOS maps, "
+                               "gain 2.1, 1 chain; reference = the C oracle on a 128x128 crop, one chain "
+                               "per host core, 1 sweep per step"},
+        "cpu_baseline": {"value": v, "unit": "pixel-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{CROP}x{CROP} crop of the 512x512 frame, 1 sweep per core per step"},
+        "e2e": {"value": v, "unit": "pixel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--fp64-sweeps", type=int, default=20)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * bdecon.h -- C ABI of libbdecon: GB300 (sm_103a) posterior sampling for
+ * Bayesian deconvolution of microscopy frames (Hendrix et al., "Re-thinking
+ * Richardson-Lucy without Iteration Cutoffs: Physically Motivated Bayesian
+ * Deconvolution", arXiv 2411.00991).
+ *
+ * The library samples the posterior of Eq. 9 over a strictly positive
+ * object rho on the camera grid padded by the PSF radius R (Fig. 5b):
+ *   likelihood  Eq. 1-6: mu = PSF (x) rho integrated over each pixel, photon
+ *               counts Poisson(mu_n) summed out against the sCMOS readout
+ *               Normal(G_n phi + o_n, var_n);
+ *   prior       Eq. 7-8: Dirichlet on |F(rho)| / sum|F(rho)| with
+ *               hyperparameter |OTF| / sum|OTF|, taken per stride x stride
+ *               patch aligned with the sub-lattice (the paper's locality
+ *               argument, Methods "Parallelization Technique");
+ *   sampler     one Metropolis-Hastings step per object pixel per sweep
+ *               (the pixel-wise Gibbs scan of Fig. 5d), pixels of one
+ *               sub-lattice class (i mod S, j mod S) updated in parallel,
+ *               classes in raster order; log-space Gaussian random-walk
+ *               proposals from Philox4x32-10 keyed by (seed) with counter
+ *               (pixel, sweep, chain, 0).
+ * The estimator is the mean of the post-burn-in samples (Results; Methods
+ * after Eq. 9).
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a bdecon_status; nothing aborts the process.
+ *     bdecon_last_error(handle) returns a message for the last failure on
+ *     that handle (for handle-less failures pass NULL: thread-local).
+ *   - "host" pointers are ordinary CPU memory, read or written before the
+ *     call returns.  Work is queued on the CUDA stream given at creation;
+ *     calls that return data to the host synchronise that stream first.
+ *   - Images are row-major, row index first.  Object arrays are
+ *     (H + 2R) x (W + 2R) with R = (L - 1) / 2.
+ *   - The handle owns all device memory it allocates (or borrows the
+ *     caller's workspace, see bdecon_create_in); bdecon_destroy frees it.
+ *   - Device-side failures (a sub-lattice wait that timed out, a
+ *     non-finite expected image) set a flag that the next bdecon_sync (or
+ *     any call that reads results) returns as BDECON_ERR_TIMEOUT or
+ *     BDECON_ERR_NUMERIC; the handle then refuses further sweeps.
+ */
+#ifndef BDECON_H
+#define BDECON_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bdecon_handle bdecon_handle;
+
+typedef enum {
+    BDECON_OK = 0,
+    BDECON_ERR_INVALID = 1,   /* bad argument; nothing was changed          */
+    BDECON_ERR_NOMEM = 2,     /* device memory (or caller workspace) short  */
+    BDECON_ERR_CUDA = 3,      /* a CUDA runtime call failed                 */
+    BDECON_ERR_TIMEOUT = 4,   /* a bounded device-side wait gave up         */
+    BDECON_ERR_STATE = 5,     /* call not allowed in the handle's state     */
+    BDECON_ERR_NUMERIC = 6    /* non-finite value met on the device         */
+} bdecon_status;
+
+typedef enum {
+    BDECON_FP64 = 0,          /* plain sampler, all arithmetic in double    */
+    BDECON_FP32 = 1           /* float sweeps; double refresh and trace     */
+} bdecon_precision;
+
+/* One deconvolution problem (a camera frame and its calibration).  All
+ * pointers are host pointers, copied by the create call.                   */
+typedef struct {
+    int32_t H, W;              /* frame size, >= 1                                  */
+    const float* image;        /* H*W readout w_n in ADU (Eq. 4)                    */
+    int32_t L;                 /* PSF side, odd, 1 <= L <= 63                       */
+    const double* psf;         /* L*L pixel-integrated PSF, >= 0, sum > 0; the
+                                  library normalises it to sum 1 (Eq. 1-2)          */
+    const float* gain_map;     /* H*W gain G_n (ADU/photon) or NULL -> gain         */
+    double gain;
+    const float* offset_map;   /* H*W offset o_n (ADU) or NULL -> offset            */
+    double offset;
+    const float* var_map;      /* H*W read-noise variance (ADU^2) or NULL -> read_var */
+    double read_var;
+    int32_t stride;            /* sub-lattice stride = prior patch side S; 0 -> L;
+                                  must be >= L.  Part of the model (it sets the
+                                  prior's patches).                                 */
+    int32_t n_chains;          /* independent chains, >= 1                          */
+    uint64_t seed;             /* Philox key                                        */
+    double step;               /* sd of the log-space random walk; 0 -> 0.2         */
+    int32_t burn_in;           /* sweeps t <= burn_in are not averaged              */
+    int32_t refresh_every;     /* recompute mu, spectra and log posterior from rho
+                                  in double every this many sweeps (0 -> never
+                                  after creation)                                   */
+    int32_t precision;         /* bdecon_precision                                  */
+    int32_t max_sweeps;        /* capacity of the per-sweep trace; 0 -> 4096        */
+    int32_t flags;             /* BDECON_FLAG_*                                     */
+} bdecon_problem;
+
+#define BDECON_FLAG_ACCEPT_LOG 1   /* keep the accept decision of every update of
+                                      every sweep (max_sweeps x object bytes; testing) */
+#define BDECON_FLAG_SECOND_MOMENT 2 /* also accumulate sum of rho^2 (uncertainty)  */
+
+/* ------------------------------------------------------------- lifetime */
+
+/* Bytes of device workspace bdecon_create_in needs for these problems.     */
+bdecon_status bdecon_workspace_size(const bdecon_problem* problems, int32_t n_problems,
+                                    size_t* bytes);
+
+/* Create a sampler over one problem.  Validates the inputs, copies them to
+ * the device (host -> device), normalises the PSF, derives the Dirichlet
+ * hyperparameters and per-pixel constants, draws the initial object
+ * (rho0_m = b0 exp(z_m / 10) with b0 = max(0.1, mean_n (w_n - o_n)/G_n) and
+ * z_m the Philox normal of counter (m, 0, chain, 0)) and runs the double-
+ * precision refresh (Eq. 1-2, 8, 9).  stream: a cudaStream_t or NULL.
+ * On failure *out is NULL and nothing stays allocated.                     */
+bdecon_status bdecon_create(const bdecon_problem* problem, void* stream, bdecon_handle** out);
+
+/* Same for a batch of problems that share every launch (one persistent
+ * sweep kernel covers all chains of all problems).                         */
+bdecon_status bdecon_batch_create(const bdecon_problem* problems, int32_t n_problems,
+                                  void* stream, bdecon_handle** out);
+
+/* As bdecon_batch_create, placing all device state in the caller's device
+ * buffer (at least bdecon_workspace_size bytes, 256-byte aligned).  The
+ * caller keeps ownership and must keep it alive until bdecon_destroy.      */
+bdecon_status bdecon_create_in(const bdecon_problem* problems, int32_t n_problems, void* stream,
+                               void* device_workspace, size_t bytes, bdecon_handle** out);
+
+void bdecon_destroy(bdecon_handle* h);
+
+const char* bdecon_last_error(const bdecon_handle* h);
+
+/* --------------------------------------------------------------- sampling */
+
+/* Queue n sweeps of every chain (asynchronous on the handle's stream).  A
+ * sweep visits the S*S sub-lattice classes in raster order of the in-patch
+ * offset (u, v); every pixel of a class is updated once.  After sweep t the
+ * object is added to the running sum when t > burn_in, and mu, the patch
+ * spectra and the log posterior are recomputed in double when t is a
+ * multiple of refresh_every.  Errors: BDECON_ERR_STATE after a device
+ * failure, BDECON_ERR_INVALID if the trace capacity would be exceeded.     */
+bdecon_status bdecon_sweep(bdecon_handle* h, int32_t n);
+
+/* Wait for queued work; returns the device error flag, if any.             */
+bdecon_status bdecon_sync(bdecon_handle* h);
+
+/* ---------------------------------------------------------------- results */
+
+/* Posterior mean of problem p over all its chains and all sweeps t >
+ * burn_in so far, in double, into host out: (H+2R)*(W+2R) values, or the
+ * H*W central crop when crop != 0.  BDECON_ERR_STATE if no sweep has been
+ * averaged yet.                                                            */
+bdecon_status bdecon_posterior_mean(bdecon_handle* h, int32_t p, double* out, int32_t crop);
+
+/* Per-pixel posterior variance (needs BDECON_FLAG_SECOND_MOMENT), same
+ * layout and pooling as bdecon_posterior_mean.                             */
+bdecon_status bdecon_posterior_var(bdecon_handle* h, int32_t p, double* out, int32_t crop);
+
+/* Log posterior (Eq. 9 without the constant log B(alpha) terms) of chain c
+ * of problem p after each sweep so far, into host out (capacity cap);
+ * *n receives the number of sweeps.  Between refreshes the value is the
+ * double running sum of the accepted changes (dL + dP); at each refresh it
+ * is the double evaluation of the state.                                   */
+bdecon_status bdecon_log_posterior_trace(bdecon_handle* h, int32_t p, int32_t c, double* out,
+                                         size_t cap, size_t* n);
+
+/* Accepted updates of chain c of problem p in each sweep so far.           */
+bdecon_status bdecon_accept_counts(bdecon_handle* h, int32_t p, int32_t c, int64_t* out,
+                                   size_t cap, size_t* n);
+
+/* Accept decisions (1/0) of every update of chain c of problem p in every
+ * sweep so far, [sweep][object pixel]; needs BDECON_FLAG_ACCEPT_LOG.  cap is
+ * in bytes; *n receives sweeps * (H+2R) * (W+2R).                          */
+bdecon_status bdecon_accept_log(bdecon_handle* h, int32_t p, int32_t c, uint8_t* out, size_t cap,
+                                size_t* n);
+
+/* Current object of chain c (host double, (H+2R)*(W+2R)) and the number of
+ * sweeps done.                                                              */
+bdecon_status bdecon_get_state(bdecon_handle* h, int32_t p, int32_t c, double* rho,
+                               int64_t* sweeps);
+
+/* Replace the object of chain c (all values > 0 and finite) and its sweep
+ * counter, then refresh mu, spectra and log posterior in double.  The
+ * running sums are cleared.  This is exact resume from a checkpoint: the
+ * random numbers depend only on (seed, pixel, sweep, chain).               */
+bdecon_status bdecon_set_state(bdecon_handle* h, int32_t p, int32_t c, const double* rho,
+                               int64_t sweeps);
+
+/* Current incrementally maintained expected image mu of chain c (H*W).      */
+bdecon_status bdecon_get_mu(bdecon_handle* h, int32_t p, int32_t c, double* mu);
+
+/* Double evaluation of Eq. 9 at the current object of chain c, without
+ * changing any state.                                                       */
+bdecon_status bdecon_log_posterior(bdecon_handle* h, int32_t p, int32_t c, double* out);
+
+/* The sweep kernel's own arithmetic (in the handle's precision) for one
+ * hypothetical update of object pixel m of chain c to rho_new, at the
+ * current state: likelihood change dL (Eq. 6 over the PSF window), prior
+ * change dP (Eq. 8 for the pixel's patch) and whether the proposal is
+ * possible (all new mu > 0 and no new spectrum coefficient exactly 0).     */
+bdecon_status bdecon_delta(bdecon_handle* h, int32_t p, int32_t c, int64_t m, double rho_new,
+                           double* dL, double* dP, int32_t* ok);
+
+/* ------------------------------------------------------------- scheduling */
+
+/* Override the launch plan of problem p: tile = tile_i x tile_j patches
+ * per thread block, warps per block.  Any plan gives bit-identical results
+ * (each update's arithmetic and reduction order are fixed by L alone); a
+ * plan whose blocks cannot all be resident is refused with
+ * BDECON_ERR_INVALID.  tile_i = 0 restores the automatic plan.             */
+bdecon_status bdecon_set_plan(bdecon_handle* h, int32_t p, int32_t tile_i, int32_t tile_j,
+                              int32_t warps);
+
+/* Launch plan in use: blocks of the sweep kernel, warps per block, tile
+ * shape of problem p.                                                       */
+bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int32_t* warps,
+                              int32_t* tile_i, int32_t* tile_j);
+
+/* Kernel launches issued by this handle since creation.                    */
+bdecon_status bdecon_launch_count(const bdecon_handle* h, int64_t* launches);
+
+/* Per-kernel timing: while enabled, CUDA events on the handle's stream
+ * bracket every launch of the sweep kernel.  bdecon_sweep_kernel_time
+ * synchronises, returns the summed device time (ms) and the number of
+ * launches measured since the last call, and resets both.                  */
+bdecon_status bdecon_set_timing(bdecon_handle* h, int32_t enable);
+bdecon_status bdecon_sweep_kernel_time(bdecon_handle* h, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDECON_H */

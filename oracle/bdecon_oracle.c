@@ -447,6 +447,66 @@ int or_delta(const or_problem* P, const double* rho, int m, double rho_new, doub
     return ok;
 }
 
+/* One update of object pixel m at sweep t evaluated from the given state
+ * using only local quantities: mu on the pixel's PSF window by Eq. 1-2 and
+ * the spectrum of the pixel's own patch by its DFT, so it costs O(L^4 + S^4)
+ * whatever the frame size.  Outputs the accept decision, the proposed value,
+ * dL and dP (0 and 0 when the proposal is impossible).  For the first class
+ * of a sweep started from rho this is exactly what the sampler does.       */
+int or_single_update(const or_problem* P, const double* rho, int m, int t, int* accept,
+                     double* rho_new, double* dL, double* dP)
+{
+    const int H = P->H, W = P->W, L = P->L, R = L / 2, S = P->S;
+    const int Ho = H + 2 * R, Wo = W + 2 * R;
+    const int i = m / Wo, j = m % Wo;
+    double* K = (double*)malloc((size_t)L * L * sizeof(double));
+    normalised_psf(P, K);
+    double z, u;
+    or_draw(P->seed, (uint32_t)m, (uint32_t)t, (uint32_t)P->chain, &z, &u);
+    const double rn = rho[m] * exp(P->step * z);
+    const double delta = rn - rho[m];
+    int ok = 1;
+    double l = 0.0;
+    for (int a = i - 2 * R; a <= i; ++a) {
+        if (a < 0 || a >= H) continue;
+        for (int b = j - 2 * R; b <= j; ++b) {
+            if (b < 0 || b >= W) continue;
+            double mu = 0.0;
+            for (int p = 0; p < L; ++p)
+                for (int q = 0; q < L; ++q)
+                    mu += K[p * L + q] * rho[(a + 2 * R - p) * Wo + (b + 2 * R - q)];
+            const int n = a * W + b;
+            const double mu_new = mu + delta * K[(a - i + 2 * R) * L + (b - j + 2 * R)];
+            if (!(mu_new > 0.0)) { ok = 0; continue; }
+            l += or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu_new)
+               - or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu);
+        }
+    }
+    const int pi = i / S, pj = j / S, i0 = pi * S, j0 = pj * S;
+    const int ph = patch_len(i0, S, Ho), pw = patch_len(j0, S, Wo), n = ph * pw;
+    double* re = (double*)malloc((size_t)n * sizeof(double));
+    double* im = (double*)malloc((size_t)n * sizeof(double));
+    double* re2 = (double*)malloc((size_t)n * sizeof(double));
+    double* im2 = (double*)malloc((size_t)n * sizeof(double));
+    double* al = (double*)malloc((size_t)n * sizeof(double));
+    double* x = (double*)malloc((size_t)n * sizeof(double));
+    for (int uu = 0; uu < ph; ++uu)
+        for (int vv = 0; vv < pw; ++vv) x[uu * pw + vv] = rho[(i0 + uu) * Wo + j0 + vv];
+    or_patch_dft(x, pw, ph, pw, re, im);
+    x[(i - i0) * pw + (j - j0)] = rn;
+    or_patch_dft(x, pw, ph, pw, re2, im2);
+    or_alpha(K, L, ph, pw, al);
+    for (int k = 0; k < n; ++k)
+        if (re2[k] == 0.0 && im2[k] == 0.0) ok = 0;
+    const double pr = ok ? or_log_prior_patch(re2, im2, al, n) - or_log_prior_patch(re, im, al, n) : 0.0;
+    *accept = ok && (log(u) < l + pr + P->step * z);
+    *rho_new = rn;
+    *dL = ok ? l : 0.0;
+    *dP = pr;
+    free(K); free(re); free(im); free(re2); free(im2); free(al); free(x);
+    return ok;
+}
+
 /* Run sweeps t0+1 .. t0+T of one chain.
  *   rho_in    starting object (NULL: the initial object of or_init)
  *   order     0: raster order inside a class; 1: reversed (for the

@@ -68,6 +68,8 @@ def lib():
                              C.c_void_p, C.c_void_p, C.c_void_p, ip, C.c_void_p, C.c_void_p,
                              C.c_void_p, C.c_void_p]
         L.or_run.restype = C.c_int
+        L.or_single_update.argtypes = [C.POINTER(OrProblem), C.c_void_p, C.c_int, C.c_int, ip, dp, dp, dp]
+        L.or_single_update.restype = C.c_int
         _lib = L
     return _lib
 
@@ -169,6 +171,14 @@ class Oracle:
         dl, dp = C.c_double(), C.c_double()
         ok = lib().or_delta(C.byref(self.c), _p(rho), int(m), float(rho_new), C.byref(dl), C.byref(dp))
         return bool(ok), dl.value, dp.value
+
+    def single_update(self, rho: np.ndarray, m: int, t: int):
+        """(accept, rho_new, dL, dP) of one update from state rho, local quantities only."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        acc, rn, dl, dp = C.c_int(), C.c_double(), C.c_double(), C.c_double()
+        lib().or_single_update(C.byref(self.c), _p(rho), int(m), int(t), C.byref(acc), C.byref(rn),
+                               C.byref(dl), C.byref(dp))
+        return bool(acc.value), rn.value, dl.value, dp.value
 
     def run(self, T: int, t0: int = 0, rho_in: Optional[np.ndarray] = None, order: int = 0,
             want_acc_log: bool = False, want_samples: bool = False):

@@ -1,0 +1,293 @@
+"""ctypes binding of libbdecon (include/bdecon.h): argument marshalling only.
+
+Every step of the sampler runs in the library's CUDA kernels; this module
+converts numpy arrays to the C structs, passes the CUDA stream, and turns
+status codes into exceptions.  It fails loudly when the library cannot be
+loaded: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+BDECON_FP64 = 0
+BDECON_FP32 = 1
+FLAG_ACCEPT_LOG = 1
+FLAG_SECOND_MOMENT = 2
+
+STATUS = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "TIMEOUT", 5: "STATE", 6: "NUMERIC"}
+
+
+class BdeconError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"bdecon {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Problem(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("image", C.c_void_p),
+                ("L", C.c_int32), ("psf", C.c_void_p),
+                ("gain_map", C.c_void_p), ("gain", C.c_double),
+                ("offset_map", C.c_void_p), ("offset", C.c_double),
+                ("var_map", C.c_void_p), ("read_var", C.c_double),
+                ("stride", C.c_int32), ("n_chains", C.c_int32), ("seed", C.c_uint64),
+                ("step", C.c_double), ("burn_in", C.c_int32), ("refresh_every", C.c_int32),
+                ("precision", C.c_int32), ("max_sweeps", C.c_int32), ("flags", C.c_int32)]
+
+
+EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bdecon_create_in",
+           "bdecon_destroy", "bdecon_last_error", "bdecon_sweep", "bdecon_sync",
+           "bdecon_posterior_mean", "bdecon_posterior_var", "bdecon_log_posterior_trace",
+           "bdecon_accept_counts", "bdecon_accept_log", "bdecon_get_state", "bdecon_set_state",
+           "bdecon_get_mu", "bdecon_log_posterior", "bdecon_delta", "bdecon_set_plan",
+           "bdecon_get_plan", "bdecon_launch_count", "bdecon_set_timing", "bdecon_sweep_kernel_time"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libbdecon.so (building it in-tree first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libbdecon.so not found at {_build.LIB}; run __graft_entry__.build()")
+    L = C.CDLL(_build.LIB)
+    vp, i32, i64, sz, dp = C.c_void_p, C.c_int32, C.c_int64, C.c_size_t, C.POINTER(C.c_double)
+    P = C.POINTER(_Problem)
+    H = C.c_void_p
+    sig = {
+        "bdecon_workspace_size": [P, i32, C.POINTER(sz)],
+        "bdecon_create": [P, vp, C.POINTER(H)],
+        "bdecon_batch_create": [P, i32, vp, C.POINTER(H)],
+        "bdecon_create_in": [P, i32, vp, vp, sz, C.POINTER(H)],
+        "bdecon_sweep": [H, i32],
+        "bdecon_sync": [H],
+        "bdecon_posterior_mean": [H, i32, vp, i32],
+        "bdecon_posterior_var": [H, i32, vp, i32],
+        "bdecon_log_posterior_trace": [H, i32, i32, vp, sz, C.POINTER(sz)],
+        "bdecon_accept_counts": [H, i32, i32, vp, sz, C.POINTER(sz)],
+        "bdecon_accept_log": [H, i32, i32, vp, sz, C.POINTER(sz)],
+        "bdecon_get_state": [H, i32, i32, vp, C.POINTER(i64)],
+        "bdecon_set_state": [H, i32, i32, vp, i64],
+        "bdecon_get_mu": [H, i32, i32, vp],
+        "bdecon_log_posterior": [H, i32, i32, dp],
+        "bdecon_delta": [H, i32, i32, i64, C.c_double, dp, dp, C.POINTER(i32)],
+        "bdecon_set_plan": [H, i32, i32, i32, i32],
+        "bdecon_get_plan": [H, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)],
+        "bdecon_launch_count": [H, C.POINTER(i64)],
+        "bdecon_set_timing": [H, i32],
+        "bdecon_sweep_kernel_time": [H, dp, C.POINTER(i64)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    L.bdecon_destroy.argtypes = [H]
+    L.bdecon_destroy.restype = None
+    L.bdecon_last_error.argtypes = [H]
+    L.bdecon_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _p(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _as_map_or_scalar(v, H, W):
+    if np.isscalar(v):
+        return None, float(v)
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+    if a.shape != (H, W):
+        raise ValueError(f"map shape {a.shape} != {(H, W)}")
+    return a, 0.0
+
+
+class Sampler:
+    """A libbdecon handle over one or more problems (``synth.Problem``-like
+    objects with image, psf, gain, offset, var, stride, n_chains, seed, step,
+    burn_in, refresh_every)."""
+
+    def __init__(self, problems, precision: int = BDECON_FP32, max_sweeps: int = 4096,
+                 flags: int = 0, stream: Optional[int] = None, workspace=None):
+        self.L = load()
+        if not isinstance(problems, (list, tuple)):
+            problems = [problems]
+        self.problems = list(problems)
+        self._keep = []
+        arr = (_Problem * len(problems))()
+        for k, pr in enumerate(problems):
+            img = np.ascontiguousarray(np.asarray(pr.image, dtype=np.float32))
+            psf = np.ascontiguousarray(np.asarray(pr.psf, dtype=np.float64))
+            H, W = img.shape
+            g, gs = _as_map_or_scalar(pr.gain, H, W)
+            o, os_ = _as_map_or_scalar(pr.offset, H, W)
+            v, vs = _as_map_or_scalar(pr.var, H, W)
+            self._keep += [img, psf, g, o, v]
+            arr[k] = _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
+                              int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
+                              int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
+                              int(flags))
+        self._arr = arr
+        self.precision = precision
+        h = C.c_void_p()
+        st = C.c_void_p(stream) if stream else None
+        if workspace is not None:
+            ptr, nbytes = workspace
+            s = self.L.bdecon_create_in(arr, len(problems), st, C.c_void_p(ptr), nbytes, C.byref(h))
+        else:
+            s = self.L.bdecon_batch_create(arr, len(problems), st, C.byref(h))
+        if s != 0:
+            raise BdeconError(s, self.L.bdecon_last_error(None).decode())
+        self.h = h
+        self._keep = []   # inputs were copied by the library
+
+    @staticmethod
+    def workspace_size(problems, precision=BDECON_FP32, max_sweeps=4096, flags=0) -> int:
+        L = load()
+        if not isinstance(problems, (list, tuple)):
+            problems = [problems]
+        keep = []
+        arr = (_Problem * len(problems))()
+        for k, pr in enumerate(problems):
+            img = np.ascontiguousarray(np.asarray(pr.image, dtype=np.float32))
+            psf = np.ascontiguousarray(np.asarray(pr.psf, dtype=np.float64))
+            H, W = img.shape
+            g, gs = _as_map_or_scalar(pr.gain, H, W)
+            o, os_ = _as_map_or_scalar(pr.offset, H, W)
+            v, vs = _as_map_or_scalar(pr.var, H, W)
+            keep += [img, psf, g, o, v]
+            arr[k] = _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
+                              int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
+                              int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
+                              int(flags))
+        n = C.c_size_t()
+        s = L.bdecon_workspace_size(arr, len(problems), C.byref(n))
+        if s != 0:
+            raise BdeconError(s, L.bdecon_last_error(None).decode())
+        return int(n.value)
+
+    # ----------------------------------------------------------- plumbing --
+    def _ck(self, s):
+        if s != 0:
+            raise BdeconError(s, self.L.bdecon_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.bdecon_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shape(self, p):
+        pr = self.problems[p]
+        H, W = np.asarray(pr.image).shape
+        R = np.asarray(pr.psf).shape[0] // 2
+        return H, W, H + 2 * R, W + 2 * R
+
+    # ----------------------------------------------------------- sampling --
+    def sweep(self, n: int):
+        self._ck(self.L.bdecon_sweep(self.h, int(n)))
+
+    def sync(self):
+        self._ck(self.L.bdecon_sync(self.h))
+
+    def posterior_mean(self, p: int = 0, crop: bool = False) -> np.ndarray:
+        H, W, Ho, Wo = self._shape(p)
+        out = np.empty((H, W) if crop else (Ho, Wo))
+        self._ck(self.L.bdecon_posterior_mean(self.h, p, _p(out), int(crop)))
+        return out
+
+    def posterior_var(self, p: int = 0, crop: bool = False) -> np.ndarray:
+        H, W, Ho, Wo = self._shape(p)
+        out = np.empty((H, W) if crop else (Ho, Wo))
+        self._ck(self.L.bdecon_posterior_var(self.h, p, _p(out), int(crop)))
+        return out
+
+    def trace(self, p: int = 0, c: int = 0) -> np.ndarray:
+        n = C.c_size_t()
+        self._ck(self.L.bdecon_log_posterior_trace(self.h, p, c, None, 0, C.byref(n)))
+        out = np.empty(n.value)
+        self._ck(self.L.bdecon_log_posterior_trace(self.h, p, c, _p(out), out.size, C.byref(n)))
+        return out
+
+    def accept_counts(self, p: int = 0, c: int = 0) -> np.ndarray:
+        n = C.c_size_t()
+        self._ck(self.L.bdecon_accept_counts(self.h, p, c, None, 0, C.byref(n)))
+        out = np.empty(n.value, dtype=np.int64)
+        self._ck(self.L.bdecon_accept_counts(self.h, p, c, _p(out), out.size, C.byref(n)))
+        return out
+
+    def accept_log(self, p: int = 0, c: int = 0) -> np.ndarray:
+        H, W, Ho, Wo = self._shape(p)
+        n = C.c_size_t()
+        self._ck(self.L.bdecon_accept_log(self.h, p, c, None, 0, C.byref(n)))
+        out = np.empty(n.value, dtype=np.uint8)
+        self._ck(self.L.bdecon_accept_log(self.h, p, c, _p(out), out.size, C.byref(n)))
+        return out.reshape(-1, Ho, Wo)
+
+    def get_state(self, p: int = 0, c: int = 0):
+        H, W, Ho, Wo = self._shape(p)
+        rho = np.empty((Ho, Wo))
+        t = C.c_int64()
+        self._ck(self.L.bdecon_get_state(self.h, p, c, _p(rho), C.byref(t)))
+        return rho, int(t.value)
+
+    def set_state(self, rho: np.ndarray, sweeps: int, p: int = 0, c: int = 0):
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        self._ck(self.L.bdecon_set_state(self.h, p, c, _p(rho), int(sweeps)))
+
+    def get_mu(self, p: int = 0, c: int = 0) -> np.ndarray:
+        H, W, Ho, Wo = self._shape(p)
+        mu = np.empty((H, W))
+        self._ck(self.L.bdecon_get_mu(self.h, p, c, _p(mu)))
+        return mu
+
+    def log_posterior(self, p: int = 0, c: int = 0) -> float:
+        v = C.c_double()
+        self._ck(self.L.bdecon_log_posterior(self.h, p, c, C.byref(v)))
+        return v.value
+
+    def delta(self, m: int, rho_new: float, p: int = 0, c: int = 0):
+        dl, dp, ok = C.c_double(), C.c_double(), C.c_int32()
+        self._ck(self.L.bdecon_delta(self.h, p, c, int(m), float(rho_new), C.byref(dl), C.byref(dp),
+                                     C.byref(ok)))
+        return bool(ok.value), dl.value, dp.value
+
+    def set_plan(self, tile_i: int, tile_j: int, warps: int, p: int = 0):
+        self._ck(self.L.bdecon_set_plan(self.h, p, int(tile_i), int(tile_j), int(warps)))
+
+    def get_plan(self, p: int = 0):
+        b, w, ti, tj = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+        self._ck(self.L.bdecon_get_plan(self.h, p, C.byref(b), C.byref(w), C.byref(ti), C.byref(tj)))
+        return dict(blocks=b.value, warps=w.value, tile_i=ti.value, tile_j=tj.value)
+
+    def set_timing(self, enable: bool = True):
+        self._ck(self.L.bdecon_set_timing(self.h, int(bool(enable))))
+
+    def sweep_kernel_time(self):
+        """(summed device ms, launches) of the sweep kernel since the last call."""
+        ms, n = C.c_double(), C.c_int64()
+        self._ck(self.L.bdecon_sweep_kernel_time(self.h, C.byref(ms), C.byref(n)))
+        return ms.value, int(n.value)
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self._ck(self.L.bdecon_launch_count(self.h, C.byref(n)))
+        return int(n.value)

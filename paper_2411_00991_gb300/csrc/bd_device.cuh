@@ -1,0 +1,305 @@
+// bd_device.cuh -- device helpers of the libbdecon kernels: Philox4x32-10,
+// precision traits, warp reductions, flag waits, and the per-pixel
+// likelihood change of Eq. 6 written as a ratio of photon-count sums.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "bd_internal.h"
+
+namespace bd {
+
+// ---------------------------------------------------------------- Philox --
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit multiplies with Weyl-sequence key increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// ((x >> 9) + 1/2) * 2^-23: 24 significant bits, exact in float and double.
+template <typename T>
+__device__ __forceinline__ T uniform23(uint32_t x)
+{
+    return ((T)(x >> 9) + (T)0.5) * (T)1.1920928955078125e-07;
+}
+
+// ------------------------------------------------------ precision traits --
+template <typename T> struct Prec;
+
+template <> struct Prec<float> {
+    static constexpr float kEps = 1.4901161193847656e-08f;  // 2^-26: sum truncation
+    static constexpr float kMaxExp = 80.0f;
+    static __device__ __forceinline__ float log(float x) { return logf(x); }
+    static __device__ __forceinline__ float exp(float x) { return expf(x); }
+    static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
+    static __device__ __forceinline__ float sqrt(float x) { return sqrtf(x); }
+    // photon-weight scale factors only shift relative term weights, which
+    // cancel to first order in the ratio; fast intrinsics suffice there
+    static __device__ __forceinline__ float wlog(float x) { return __logf(x); }
+    static __device__ __forceinline__ float wexp(float x) { return __expf(x); }
+    static __device__ __forceinline__ float rcp(float x)
+    {
+        float r;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    }
+    static __device__ __forceinline__ float gauss(float u0, float u1)
+    {
+        return sqrtf(-2.0f * logf(u0)) * cospif(2.0f * u1);
+    }
+};
+
+template <> struct Prec<double> {
+    static constexpr double kEps = 1.3877787807814457e-17;  // 2^-56
+    static constexpr double kMaxExp = 700.0;
+    static __device__ __forceinline__ double log(double x) { return ::log(x); }
+    static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }
+    static __device__ __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+    static __device__ __forceinline__ double wlog(double x) { return ::log(x); }
+    static __device__ __forceinline__ double wexp(double x) { return ::exp(x); }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double gauss(double u0, double u1)
+    {
+        return ::sqrt(-2.0 * ::log(u0)) * ::cos(2.0 * CUDART_PI * u1);
+    }
+};
+
+// Explicitly rounded product and sum (never contracted into an FMA), so the
+// expected-image value a proposal is scored with is bit-identical to the
+// value written when it is accepted.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <typename T> struct alignas(4 * sizeof(T)) Dat4 { T c, is2, beta, lnorm; };
+
+template <typename T> __device__ __forceinline__ const T* kern(const Image& im);
+template <> __device__ __forceinline__ const float* kern<float>(const Image& im) { return im.K32; }
+template <> __device__ __forceinline__ const double* kern<double>(const Image& im) { return im.K64; }
+template <typename T> __device__ __forceinline__ const Dat4<T>* dat(const Image& im);
+template <> __device__ __forceinline__ const Dat4<float>* dat<float>(const Image& im)
+{
+    return reinterpret_cast<const Dat4<float>*>(im.dat32);
+}
+template <> __device__ __forceinline__ const Dat4<double>* dat<double>(const Image& im)
+{
+    return reinterpret_cast<const Dat4<double>*>(im.dat64);
+}
+template <typename T> __device__ __forceinline__ const T* ent_wa(const Image& im);
+template <> __device__ __forceinline__ const float* ent_wa<float>(const Image& im) { return im.ent_wa32; }
+template <> __device__ __forceinline__ const double* ent_wa<double>(const Image& im) { return im.ent_wa64; }
+template <typename T> __device__ __forceinline__ const T* ent_m(const Image& im);
+template <> __device__ __forceinline__ const float* ent_m<float>(const Image& im) { return im.ent_m32; }
+template <> __device__ __forceinline__ const double* ent_m<double>(const Image& im) { return im.ent_m64; }
+template <typename T> __device__ __forceinline__ const T* twid(const Image& im);
+template <> __device__ __forceinline__ const float* twid<float>(const Image& im) { return im.tw32; }
+template <> __device__ __forceinline__ const double* twid<double>(const Image& im) { return im.tw64; }
+
+// ------------------------------------------------------------ warp sums --
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------ memory ordering --
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed(const int* p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait of one warp until prog[nbr[i]] >= need for every i < nn.
+// Gives up (setting kErrTimeout) after ~4 s or 2^26 polls, or as soon as any
+// other block has raised an error.  Returns true if every flag arrived.
+constexpr uint64_t kWaitNs = 4000000000ull;
+constexpr uint32_t kWaitPolls = 1u << 26;
+
+__device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr, int nn, int need,
+                                                int* err)
+{
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    if (lane < nn) {
+        const int* f = prog + nbr[lane];
+        if (ld_acquire(f) < need) {
+            const uint64_t t0 = global_ns();
+            uint32_t it = 0;
+            while (ld_acquire(f) < need) {
+                ++it;
+                if ((it & 31u) == 0u) {
+                    if (ld_relaxed(err) != 0) { ok = false; break; }
+                    if (global_ns() - t0 > kWaitNs || it > kWaitPolls) {
+                        atomicOr(err, kErrTimeout);
+                        ok = false;
+                        break;
+                    }
+                }
+                __nanosleep(20);
+            }
+        }
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// ---------------------------------------------- per-pixel likelihood change
+// Change of the log marginal likelihood of one camera pixel (Eq. 6),
+//   l(mu') - l(mu) = -(mu' - mu) + log S(mu') - log S(mu),
+//   S(mu) = sum_phi exp(-(c - phi)^2 / (2 s^2)) mu^phi / phi!,
+// with c = (w - o)/G and s^2 = var/G^2 (the photon-count form of
+// Normal(w; G phi + o, var)).  Writing r = mu'/mu and T_phi for the summand
+// at mu, S(mu')/S(mu) = r^phi0 * (B + D)/B with B = sum_phi T_phi and
+// D = sum_phi T_phi (r^(phi - phi0) - 1), so
+//   l(mu') - l(mu) = -x + phi0 log1p(x/mu) + log1p(D/B),     x = mu' - mu,
+// free of cancellation for small x.  The summand is log-concave in phi; the
+// sums run outward from phi0 (a Newton estimate of the mode) with term
+// ratios updated multiplicatively (the Gaussian factor by exp(-1/s^2) per
+// step) until terms fall below kEps of the running sum.
+template <typename T>
+__device__ __forceinline__ T dl_pixel(T mu, T x, T c, T is2, T beta, bool& bad)
+{
+    using P = Prec<T>;
+    const T mup = add_rn(mu, x);
+    if (!(mup > (T)0)) {
+        bad = true;
+        return (T)0;
+    }
+    // mode of the photon posterior: Gaussian-approximation centre, then one
+    // Newton step on d/dphi log T_phi ~ (c - phi)/s^2 + log(mu / (phi + 1/2))
+    const float muf = (float)mu, cf = (float)c, isf = (float)is2;
+    float ph = muf * (cf * isf + 1.0f) / (muf * isf + 1.0f);
+    ph = fmaxf(ph, 0.0f);
+    const float f = (cf - ph) * isf + __logf(muf / (ph + 0.5f));
+    const float fp = -isf - 1.0f / (ph + 0.5f);
+    const float phs = fminf(fmaxf(ph - f / fp, 0.0f), 1.0e7f);
+    const int p0 = __float2int_rn(phs);
+    const T fp0 = (T)p0;
+
+    const T inv_mu = P::rcp(mu);
+    const T d = x * inv_mu;              // r - 1
+    const T r = (T)1 + d;
+    const T lmu = P::wlog(mu);
+    T B = (T)1, D = (T)0;
+    // upward: T_{phi+1} = T_phi * mu exp((c - phi - 1/2)/s^2) / (phi + 1)
+    {
+        T mg = P::wexp(fmin(lmu + (c - fp0 - (T)0.5) * is2, (T)P::kMaxExp));
+        T t = (T)1, e = (T)0;
+        T fphi = fp0;
+        for (int it = 0; it < 4096; ++it) {
+            fphi += (T)1;
+            t *= mg * P::rcp(fphi);
+            mg *= beta;
+            e = fma(e, r, d);                 // r^k - 1
+            B += t;
+            D = fma(t, e, D);
+            if (t * fmax((T)1, (T)1 + e) < (T)P::kEps * B) break;
+        }
+    }
+    // downward: T_{phi-1} = T_phi * phi exp(-(c - phi + 1/2)/s^2) / mu
+    if (p0 > 0) {
+        T hq = P::wexp(fmin(-lmu - (c - fp0 + (T)0.5) * is2, (T)P::kMaxExp));
+        const T ri = P::rcp(r);
+        const T di = -d * ri;                // 1/r - 1
+        T t = (T)1, e = (T)0;
+        T fphi = fp0;
+        for (int phi = p0; phi > 0; --phi) {
+            t *= hq * fphi;
+            hq *= beta;
+            fphi -= (T)1;
+            e = fma(e, ri, di);               // r^-k - 1
+            B += t;
+            D = fma(t, e, D);
+            if (t * fmax((T)1, (T)1 + e) < (T)P::kEps * B) break;
+        }
+    }
+    return -x + fp0 * P::log1p(d) + P::log1p(D / B);
+}
+
+// Full log marginal likelihood of one camera pixel in double (Eq. 6):
+//   l(mu) = -log(2 pi var)/2 - mu + log sum_phi exp(-(c-phi)^2/(2 s^2)) mu^phi / phi!
+// evaluated as log T_phi0 + log(sum_phi T_phi / T_phi0) with the same
+// outward recurrences (truncation 2^-56).
+__device__ __forceinline__ double loglik64(double mu, double c, double is2, double beta,
+                                           double lnorm)
+{
+    const float muf = (float)mu, cf = (float)c, isf = (float)is2;
+    float ph = muf * (cf * isf + 1.0f) / (muf * isf + 1.0f);
+    ph = fmaxf(ph, 0.0f);
+    const float f = (cf - ph) * isf + __logf(muf / (ph + 0.5f));
+    const float fp = -isf - 1.0f / (ph + 0.5f);
+    const float phs = fminf(fmaxf(ph - f / fp, 0.0f), 1.0e7f);
+    const int p0 = __float2int_rn(phs);
+    const double fp0 = (double)p0;
+    const double lmu = ::log(mu);
+    const double lt0 = -0.5 * (c - fp0) * (c - fp0) * is2 + fp0 * lmu - ::lgamma(fp0 + 1.0);
+    double B = 1.0;
+    {
+        double mg = ::exp(fmin(lmu + (c - fp0 - 0.5) * is2, 700.0));
+        double t = 1.0, fphi = fp0;
+        for (int it = 0; it < 4096; ++it) {
+            fphi += 1.0;
+            t *= mg / fphi;
+            mg *= beta;
+            B += t;
+            if (t < 1.3877787807814457e-17 * B) break;
+        }
+    }
+    if (p0 > 0) {
+        double hq = ::exp(fmin(-lmu - (c - fp0 + 0.5) * is2, 700.0));
+        double t = 1.0, fphi = fp0;
+        for (int phi = p0; phi > 0; --phi) {
+            t *= hq * fphi;
+            hq *= beta;
+            fphi -= 1.0;
+            B += t;
+            if (t < 1.3877787807814457e-17 * B) break;
+        }
+    }
+    return lnorm - mu + lt0 + ::log(B);
+}
+
+// Patch shape index of patch (pi, pj): bit 1 = partial rows, bit 0 = partial columns.
+__device__ __forceinline__ int shape_index(const Image& im, int pi, int pj)
+{
+    return ((pi + 1) * im.S > im.Ho ? 2 : 0) | ((pj + 1) * im.S > im.Wo ? 1 : 0);
+}
+
+}  // namespace bd

@@ -1,0 +1,110 @@
+// bd_internal.h -- device-visible descriptors shared by the libbdecon kernels
+// and the host code that builds them.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bd {
+
+constexpr int kMaxShapes = 4;       // patch shapes: full, right, bottom, corner
+constexpr int kMaxL = 63;           // largest PSF side
+constexpr int kMaxS = 64;           // largest stride (prior patch side)
+constexpr int kMaxSlots = 64;       // sweeps per sweep-kernel launch
+constexpr int kRedThreads = 256;    // fixed block size of every reduction
+
+// device error flag bits
+constexpr int kErrTimeout = 1;
+constexpr int kErrNumeric = 2;
+
+// One patch shape (ph x pw) of a problem.  The prior of Eq. 8 is evaluated on
+// a canonical half of the frequencies: one representative of each Hermitian
+// pair {k, -k} with multiplicity 2, self-conjugate frequencies with 1.
+struct Shape {
+    int ph, pw, K, nhalf;
+    int ent_off;            // first entry in the problem's entry arrays
+    int twh_off, tww_off;   // twiddle tables exp(-2 pi i j / ph), exp(-2 pi i j / pw)
+};
+
+// One problem (frame + calibration + PSF), shared by its chains.
+struct Image {
+    int H, W, L, R, S, Ho, Wo, npi, npj;
+    int mu_pitch;                    // elements per row of mu (multiple of 4)
+    int n_chains;
+    uint32_t seed_lo, seed_hi;
+    double step;
+    int burn_in, refresh_every;
+    int n_patches;
+    int chain0;                      // index of its first chain in the chain table
+    const double* K64;               // L*L, normalised
+    const float* K32;
+    const double* dat64;             // per camera pixel {c, 1/s^2, exp(-1/s^2), -log(2 pi var)/2}
+    const float* dat32;
+    Shape shape[kMaxShapes];
+    const int* ent_kl;               // (k << 16) | l
+    const double* ent_wa64;          // mult * (alpha - 1) / 2
+    const double* ent_m64;           // mult
+    const float* ent_wa32;
+    const float* ent_m32;
+    const double* tw64;              // complex pairs
+    const float* tw32;
+    const int64_t* patch_off;        // offset (complex elements) of each patch's half spectrum
+    int64_t spec_len;                // complex elements per chain
+};
+
+// One chain (an instance of a problem with its own state and random stream).
+struct Chain {
+    int img, chain;
+    void* rho;                       // Ho*Wo, T
+    void* mu;                        // H*mu_pitch, T
+    void* spec;                      // spec_len complex T
+    double* rho_sum;                 // Ho*Wo
+    double* rho_sq;                  // Ho*Wo or null
+    double* trace_part;              // [slot][patch] accepted dL + dP
+    unsigned long long* acc_count;   // [sweep - 1]
+    uint8_t* acc_log;                // [sweep - 1][Ho*Wo] or null
+    int* prog;                       // per tile: steps completed in this launch
+    double* trace;                   // [sweep 0..max_sweeps]
+    int tpi, tpj, nti, ntj;          // tile shape (patches) and tile grid
+    int cta_base;                    // first block of this chain in the sweep grid
+};
+
+struct SweepArgs {
+    const Image* imgs;
+    const Chain* chains;
+    int n_chains;
+    int t0;                          // sweeps completed before this launch
+    int n_sweeps;                    // sweeps in this launch
+    int* err;
+};
+
+// host launchers (defined in the .cu files)
+void launch_setup(const Image& im, const Image* d_im, const float* w, const float* g,
+                  const float* o, const float* v, double gs, double os, double vs,
+                  const double* psf_raw, double* b0_out, double* scratch, cudaStream_t st,
+                  int64_t* launches);
+template <typename T>
+void launch_init_rho(const Image& im, const Chain& ch, const double* b0, cudaStream_t st,
+                     int64_t* launches);
+template <typename T>
+void launch_refresh(const Image& im, const Chain& ch, double* scratch, int write_state,
+                    double* out_logpost, int* err, cudaStream_t st, int64_t* launches);
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs& a, int grid, int warps, cudaStream_t st);
+template <typename T>
+int sweep_blocks_per_sm(int warps);
+void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int t0, int n_sweeps,
+                  cudaStream_t st, int64_t* launches);
+template <typename T>
+void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3,
+                  cudaStream_t st, int64_t* launches);
+template <typename T>
+void launch_convert(const void* src, double* dst, int64_t n, int rows, int cols, int src_pitch,
+                    cudaStream_t st, int64_t* launches);
+template <typename T>
+void launch_set_rho(const double* src, void* dst, int64_t n, cudaStream_t st, int64_t* launches);
+void launch_mean(const double* sum, int n_chains_img, int64_t chain_stride_elems, int Ho, int Wo,
+                 int crop_r, int out_h, int out_w, double inv_n, double* out, const double* sq,
+                 int want_var, cudaStream_t st, int64_t* launches);
+
+}  // namespace bd

@@ -1,0 +1,398 @@
+// bd_state.cu -- set-up, refresh and read-out kernels of libbdecon.
+//
+//   a1  set-up (double): normalised PSF (Eq. 1-2), per-pixel photon-unit
+//       constants of Eq. 4-6, Dirichlet hyperparameters |OTF| / sum |OTF| of
+//       Eq. 8 per patch shape, twiddle tables, initial object.
+//   a8  refresh (double): mu = K (x) rho by direct summation, patch spectra
+//       by direct DFT, and the full log posterior of Eq. 9; it replaces the
+//       incrementally updated mu and spectra (drift correction) and rebases
+//       the trace.
+// Every reduction uses a fixed block size and a fixed tree, so results do
+// not depend on the launch plan of the sweep kernel.
+#include <cmath>
+
+#include "bd_device.cuh"
+
+namespace bd {
+
+// deterministic block sum (kRedThreads threads)
+__device__ __forceinline__ double block_sum(double v, double* sh)
+{
+    const int tid = threadIdx.x;
+    sh[tid] = v;
+    __syncthreads();
+    for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+        if (tid < o) sh[tid] += sh[tid + o];
+        __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------ a1 ---
+__global__ void __launch_bounds__(kRedThreads) k_setup_psf(int L, const double* psf, double* K64, float* K32)
+{
+    __shared__ double sh[kRedThreads];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < L * L; k += kRedThreads) s += psf[k];
+    const double tot = block_sum(s, sh);
+    for (int k = threadIdx.x; k < L * L; k += kRedThreads) {
+        const double v = psf[k] / tot;
+        K64[k] = v;
+        K32[k] = (float)v;
+    }
+}
+
+// c = (w - o)/G, s^2 = var/G^2 (photon units), 1/s^2, exp(-1/s^2), -log(2 pi var)/2
+__global__ void __launch_bounds__(kRedThreads) k_setup_data(int n, const float* w, const float* g, const float* o,
+                                                           const float* v, double gs, double os, double vs,
+                                                           double* dat64, float* dat32, double* part_c)
+{
+    __shared__ double sh[kRedThreads];
+    const int idx = blockIdx.x * kRedThreads + threadIdx.x;
+    double c = 0.0;
+    if (idx < n) {
+        const double G = g ? (double)g[idx] : gs;
+        const double off = o ? (double)o[idx] : os;
+        const double var = v ? (double)v[idx] : vs;
+        c = ((double)w[idx] - off) / G;
+        const double is2 = G * G / var;
+        const double beta = exp(-is2);
+        const double lnorm = -0.5 * log(2.0 * CUDART_PI * var);
+        dat64[4 * (size_t)idx + 0] = c;
+        dat64[4 * (size_t)idx + 1] = is2;
+        dat64[4 * (size_t)idx + 2] = beta;
+        dat64[4 * (size_t)idx + 3] = lnorm;
+        dat32[4 * (size_t)idx + 0] = (float)c;
+        dat32[4 * (size_t)idx + 1] = (float)is2;
+        dat32[4 * (size_t)idx + 2] = (float)beta;
+        dat32[4 * (size_t)idx + 3] = (float)lnorm;
+    }
+    const double s = block_sum(c, sh);
+    if (threadIdx.x == 0) part_c[blockIdx.x] = s;
+}
+
+// b0 = max(0.1, mean_n c_n)
+__global__ void __launch_bounds__(kRedThreads) k_setup_b0(const double* part_c, int nblk, int npix, double* b0)
+{
+    __shared__ double sh[kRedThreads];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nblk; k += kRedThreads) s += part_c[k];
+    const double tot = block_sum(s, sh);
+    if (threadIdx.x == 0) {
+        const double m = tot / (double)npix;
+        b0[0] = m > 0.1 ? m : 0.1;
+    }
+}
+
+// exp(-2 pi i j / n) for j < n
+__global__ void k_setup_tw(int n, double* tw64, float* tw32)
+{
+    for (int j = threadIdx.x + blockIdx.x * blockDim.x; j < n; j += blockDim.x * gridDim.x) {
+        double s, c;
+        sincospi(2.0 * (double)j / (double)n, &s, &c);
+        tw64[2 * j] = c;
+        tw64[2 * j + 1] = -s;
+        tw32[2 * j] = (float)c;
+        tw32[2 * j + 1] = (float)-s;
+    }
+}
+
+// Eq. 8 hyperparameter for one patch shape: alpha = |DFT(PSF wrapped onto the
+// ph x pw torus, centre at the origin)| / sum, then the weights of the
+// canonical half-spectrum entries: mult * (alpha - 1) / 2 and mult.
+__global__ void __launch_bounds__(kRedThreads) k_setup_alpha(int L, const double* K64, int ph, int pw,
+                                                            const int* ent_kl, int nhalf, double* kw,
+                                                            double* mag, double* wa64, double* m64,
+                                                            float* wa32, float* m32)
+{
+    __shared__ double sh[kRedThreads];
+    const int R = L / 2, n = ph * pw;
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < n; ++k) kw[k] = 0.0;
+        for (int p = 0; p < L; ++p)
+            for (int q = 0; q < L; ++q) {
+                const int x = ((p - R) % ph + ph) % ph, y = ((q - R) % pw + pw) % pw;
+                kw[x * pw + y] += K64[p * L + q];
+            }
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int idx = threadIdx.x; idx < n; idx += kRedThreads) {
+        const int k = idx / pw, l = idx % pw;
+        double re = 0.0, im = 0.0;
+        for (int u = 0; u < ph; ++u)
+            for (int v = 0; v < pw; ++v) {
+                const double fr = (double)((k * u) % ph) / ph + (double)((l * v) % pw) / pw;
+                double s, c;
+                sincospi(2.0 * fr, &s, &c);
+                re += kw[u * pw + v] * c;
+                im -= kw[u * pw + v] * s;
+            }
+        mag[idx] = hypot(re, im);
+        part += mag[idx];
+    }
+    // the sum over all frequencies, in a fixed order
+    __syncthreads();
+    const double tot = block_sum(part, sh);
+    for (int e = threadIdx.x; e < nhalf; e += kRedThreads) {
+        const int kl = ent_kl[e];
+        const int k = kl >> 16, l = kl & 0xffff;
+        const bool self = ((ph - k) % ph == k) && ((pw - l) % pw == l);
+        const double mult = self ? 1.0 : 2.0;
+        const double a = mag[k * pw + l] / tot;
+        wa64[e] = 0.5 * mult * (a - 1.0);
+        m64[e] = mult;
+        wa32[e] = (float)wa64[e];
+        m32[e] = (float)mult;
+    }
+}
+
+// Initial object rho0_m = b0 exp(z_m / 10), z_m the Box-Muller normal of the
+// Philox counter (m, 0, chain, 0): sweep index 0 is never a sampling sweep.
+template <typename T>
+__global__ void k_init_rho(int n, uint32_t seed_lo, uint32_t seed_hi, int chain, const double* b0, T* rho)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)m, 0u, (uint32_t)chain, 0u), seed_lo, seed_hi);
+    const double z = sqrt(-2.0 * log(uniform23<double>(x.x))) * cos(2.0 * CUDART_PI * uniform23<double>(x.y));
+    rho[m] = (T)(b0[0] * exp(0.1 * z));
+}
+
+void launch_setup(const Image& im, const Image* d_im, const float* w, const float* g, const float* o,
+                  const float* v, double gs, double os, double vs, const double* psf_raw, double* b0_out,
+                  double* scratch, cudaStream_t st, int64_t* launches)
+{
+    (void)d_im;
+    k_setup_psf<<<1, kRedThreads, 0, st>>>(im.L, psf_raw, const_cast<double*>(im.K64), const_cast<float*>(im.K32));
+    const int npix = im.H * im.W;
+    const int nblk = (npix + kRedThreads - 1) / kRedThreads;
+    double* part_c = scratch;                       // nblk
+    k_setup_data<<<nblk, kRedThreads, 0, st>>>(npix, w, g, o, v, gs, os, vs, const_cast<double*>(im.dat64),
+                                               const_cast<float*>(im.dat32), part_c);
+    k_setup_b0<<<1, kRedThreads, 0, st>>>(part_c, nblk, npix, b0_out);
+    *launches += 3;
+    // twiddles: the distinct patch sides appear at the shapes' offsets
+    for (int s = 0; s < kMaxShapes; ++s) {
+        const Shape& sh = im.shape[s];
+        if (sh.nhalf == 0) continue;
+        k_setup_tw<<<1, 128, 0, st>>>(sh.ph, const_cast<double*>(im.tw64) + 2 * sh.twh_off,
+                                      const_cast<float*>(im.tw32) + 2 * sh.twh_off);
+        k_setup_tw<<<1, 128, 0, st>>>(sh.pw, const_cast<double*>(im.tw64) + 2 * sh.tww_off,
+                                      const_cast<float*>(im.tw32) + 2 * sh.tww_off);
+        double* kw = scratch + nblk + 8;
+        double* mag = kw + kMaxS * kMaxS;
+        k_setup_alpha<<<1, kRedThreads, 0, st>>>(im.L, im.K64, sh.ph, sh.pw, im.ent_kl + sh.ent_off, sh.nhalf, kw,
+                                                 mag, const_cast<double*>(im.ent_wa64) + sh.ent_off,
+                                                 const_cast<double*>(im.ent_m64) + sh.ent_off,
+                                                 const_cast<float*>(im.ent_wa32) + sh.ent_off,
+                                                 const_cast<float*>(im.ent_m32) + sh.ent_off);
+        *launches += 3;
+    }
+}
+
+template <typename T>
+void launch_init_rho(const Image& im, const Chain& ch, const double* b0, cudaStream_t st, int64_t* launches)
+{
+    const int n = im.Ho * im.Wo;
+    k_init_rho<T><<<(n + 255) / 256, 256, 0, st>>>(n, im.seed_lo, im.seed_hi, ch.chain, b0, reinterpret_cast<T*>(ch.rho));
+    ++*launches;
+}
+template void launch_init_rho<float>(const Image&, const Chain&, const double*, cudaStream_t, int64_t*);
+template void launch_init_rho<double>(const Image&, const Chain&, const double*, cudaStream_t, int64_t*);
+
+// ------------------------------------------------------------------ a8 ---
+// mu = K (x) rho (Eq. 1-2) and the per-pixel log likelihood (Eq. 6), double.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_refresh_mu(Image im, Chain ch, double* part_ll, int write,
+                                                           int* err)
+{
+    __shared__ double sh[kRedThreads];
+    const int idx = blockIdx.x * kRedThreads + threadIdx.x;
+    double ll = 0.0;
+    if (idx < im.H * im.W) {
+        const int a = idx / im.W, b = idx % im.W;
+        const T* rho = reinterpret_cast<const T*>(ch.rho);
+        const int L = im.L, R = im.R;
+        double mu = 0.0;
+        for (int p = 0; p < L; ++p) {
+            const T* row = rho + (size_t)(a + 2 * R - p) * im.Wo + (b + 2 * R);
+            for (int q = 0; q < L; ++q) mu += im.K64[p * L + q] * (double)row[-q];
+        }
+        if (!(mu > 0.0) || !isfinite(mu)) {
+            atomicOr(err, kErrNumeric);
+        } else {
+            const double* d = im.dat64 + 4 * (size_t)idx;
+            ll = loglik64(mu, d[0], d[1], d[2], d[3]);
+        }
+        if (write) reinterpret_cast<T*>(ch.mu)[(size_t)a * im.mu_pitch + b] = (T)mu;
+    }
+    const double s = block_sum(ll, sh);
+    if (threadIdx.x == 0) part_ll[blockIdx.x] = s;
+}
+
+// Patch spectra by direct DFT (canonical half) and the patch log prior of Eq. 8:
+//   sum_e mult_e (alpha_e - 1) log|X_e| + (K - 1) log sum_e mult_e |X_e|.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_refresh_spec(Image im, Chain ch, double* part_lp, int write)
+{
+    __shared__ double sh[kRedThreads];
+    const int p = blockIdx.x;
+    const int pi = p / im.npj, pj = p % im.npj;
+    const Shape& sp = im.shape[shape_index(im, pi, pj)];
+    const T* rho = reinterpret_cast<const T*>(ch.rho) + (size_t)pi * im.S * im.Wo + pj * im.S;
+    const double2* twh = reinterpret_cast<const double2*>(im.tw64) + sp.twh_off;
+    const double2* tww = reinterpret_cast<const double2*>(im.tw64) + sp.tww_off;
+    using T2 = typename Vec2<T>::type;
+    T2* spec = reinterpret_cast<T2*>(ch.spec) + im.patch_off[p];
+    double sl = 0.0, sm = 0.0;
+    for (int e = threadIdx.x; e < sp.nhalf; e += kRedThreads) {
+        const int kl = im.ent_kl[sp.ent_off + e];
+        const int k = kl >> 16, l = kl & 0xffff;
+        double re = 0.0, imv = 0.0;
+        for (int u = 0; u < sp.ph; ++u) {
+            const double2 eh = twh[(k * u) % sp.ph];
+            for (int v = 0; v < sp.pw; ++v) {
+                const double2 ew = tww[(l * v) % sp.pw];
+                const double wr = eh.x * ew.x - eh.y * ew.y, wi = eh.x * ew.y + eh.y * ew.x;
+                const double x = (double)rho[(size_t)u * im.Wo + v];
+                re += x * wr;
+                imv += x * wi;
+            }
+        }
+        if (write) {
+            T2 X;
+            X.x = (T)re;
+            X.y = (T)imv;
+            spec[e] = X;
+        }
+        const double n2 = re * re + imv * imv;
+        sl += im.ent_wa64[sp.ent_off + e] * log(n2);
+        sm += im.ent_m64[sp.ent_off + e] * sqrt(n2);
+    }
+    const double tl = block_sum(sl, sh);
+    const double tm = block_sum(sm, sh);
+    if (threadIdx.x == 0) part_lp[p] = tl + (double)(sp.K - 1) * log(tm);
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_refresh_total(const double* part_ll, int n_ll, const double* part_lp,
+                                                              int n_lp, double* out)
+{
+    __shared__ double sh[kRedThreads];
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < n_ll; k += kRedThreads) a += part_ll[k];
+    for (int k = threadIdx.x; k < n_lp; k += kRedThreads) b += part_lp[k];
+    const double ta = block_sum(a, sh);
+    const double tb = block_sum(b, sh);
+    if (threadIdx.x == 0) out[0] = ta + tb;
+}
+
+template <typename T>
+void launch_refresh(const Image& im, const Chain& ch, double* scratch, int write_state, double* out_logpost,
+                    int* err, cudaStream_t st, int64_t* launches)
+{
+    const int nblk = (im.H * im.W + kRedThreads - 1) / kRedThreads;
+    double* part_ll = scratch;
+    double* part_lp = scratch + nblk;
+    k_refresh_mu<T><<<nblk, kRedThreads, 0, st>>>(im, ch, part_ll, write_state, err);
+    k_refresh_spec<T><<<im.n_patches, kRedThreads, 0, st>>>(im, ch, part_lp, write_state);
+    k_refresh_total<<<1, kRedThreads, 0, st>>>(part_ll, nblk, part_lp, im.n_patches, out_logpost);
+    *launches += 3;
+}
+template void launch_refresh<float>(const Image&, const Chain&, double*, int, double*, int*, cudaStream_t, int64_t*);
+template void launch_refresh<double>(const Image&, const Chain&, double*, int, double*, int*, cudaStream_t, int64_t*);
+
+// ------------------------------------------------------------ trace -----
+// trace[t0 + s + 1] = trace[t0] + sum_{s' <= s} sum_p part[s'][p]: the double
+// running sum of accepted dL + dP, per chain (one block per chain).
+__global__ void __launch_bounds__(kRedThreads) k_trace(const Image* imgs, const Chain* chains, int t0, int n)
+{
+    __shared__ double sh[kRedThreads];
+    const Chain& ch = chains[blockIdx.x];
+    const int np = imgs[ch.img].n_patches;
+    double cum = ch.trace[t0];
+    for (int s = 0; s < n; ++s) {
+        double a = 0.0;
+        for (int p = threadIdx.x; p < np; p += kRedThreads) a += ch.trace_part[(size_t)s * np + p];
+        cum += block_sum(a, sh);
+        if (threadIdx.x == 0) ch.trace[t0 + s + 1] = cum;
+    }
+}
+
+void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int t0, int n_sweeps, cudaStream_t st,
+                  int64_t* launches)
+{
+    k_trace<<<n_chains, kRedThreads, 0, st>>>(d_imgs, d_chains, t0, n_sweeps);
+    ++*launches;
+}
+
+// --------------------------------------------------------- conversions --
+template <typename T>
+__global__ void k_to_double(const T* src, double* dst, int rows, int cols, int pitch)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    const int r = (int)(idx / cols), c = (int)(idx % cols);
+    dst[idx] = (double)src[(size_t)r * pitch + c];
+}
+
+template <typename T>
+void launch_convert(const void* src, double* dst, int64_t n, int rows, int cols, int src_pitch, cudaStream_t st,
+                    int64_t* launches)
+{
+    (void)n;
+    const int64_t tot = (int64_t)rows * cols;
+    k_to_double<T><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(reinterpret_cast<const T*>(src), dst, rows, cols,
+                                                                   src_pitch);
+    ++*launches;
+}
+template void launch_convert<float>(const void*, double*, int64_t, int, int, int, cudaStream_t, int64_t*);
+template void launch_convert<double>(const void*, double*, int64_t, int, int, int, cudaStream_t, int64_t*);
+
+template <typename T>
+__global__ void k_from_double(const double* src, T* dst, int64_t n)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) dst[idx] = (T)src[idx];
+}
+
+template <typename T>
+void launch_set_rho(const double* src, void* dst, int64_t n, cudaStream_t st, int64_t* launches)
+{
+    k_from_double<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, reinterpret_cast<T*>(dst), n);
+    ++*launches;
+}
+template void launch_set_rho<float>(const double*, void*, int64_t, cudaStream_t, int64_t*);
+template void launch_set_rho<double>(const double*, void*, int64_t, cudaStream_t, int64_t*);
+
+// posterior mean (and variance) pooled over the chains of one problem
+__global__ void k_mean(const double* sum, int n_chains, int64_t stride, int Wo, int crop_r, int oh, int ow,
+                       double inv_n, double* out, const double* sq, int want_var)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= oh * ow) return;
+    const int y = idx / ow + crop_r, x = idx % ow + crop_r;
+    const size_t m = (size_t)y * Wo + x;
+    double s = 0.0, q = 0.0;
+    for (int c = 0; c < n_chains; ++c) {
+        s += sum[c * stride + m];
+        if (want_var) q += sq[c * stride + m];
+    }
+    const double mean = s * inv_n;
+    out[idx] = want_var ? fmax(q * inv_n - mean * mean, 0.0) : mean;
+}
+
+void launch_mean(const double* sum, int n_chains_img, int64_t chain_stride_elems, int Ho, int Wo, int crop_r,
+                 int out_h, int out_w, double inv_n, double* out, const double* sq, int want_var, cudaStream_t st,
+                 int64_t* launches)
+{
+    (void)Ho;
+    const int n = out_h * out_w;
+    k_mean<<<(n + 255) / 256, 256, 0, st>>>(sum, n_chains_img, chain_stride_elems, Wo, crop_r, out_h, out_w, inv_n,
+                                            out, sq, want_var);
+    ++*launches;
+}
+
+}  // namespace bd

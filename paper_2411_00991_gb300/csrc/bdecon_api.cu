@@ -1,0 +1,848 @@
+// bdecon_api.cu -- host side of the libbdecon C ABI (see include/bdecon.h):
+// argument validation, the device arena, the launch plan of the persistent
+// sweep kernel, and the sweep / refresh / trace schedule.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bdecon.h"
+#include "bd_internal.h"
+
+using namespace bd;
+
+namespace {
+
+thread_local std::string g_err;
+
+struct ProbHost {
+    bdecon_problem p;           // copy (host pointers not retained)
+    int H, W, L, R, S, Ho, Wo, npi, npj, n_patches, pitch;
+    int tpi = 1, tpj = 1;       // tile shape in patches
+    bool user_plan = false;
+    int64_t n_sum = 0;          // sweeps averaged so far
+    Shape shape[kMaxShapes];
+    std::vector<int> ent_kl;
+    std::vector<int64_t> patch_off;
+    int64_t spec_len = 0;
+    int n_tw = 0;               // complex twiddle entries
+    // arena offsets (bytes)
+    size_t o_K64, o_K32, o_dat64, o_dat32, o_ekl, o_wa64, o_m64, o_wa32, o_m32, o_tw64, o_tw32, o_poff;
+    size_t o_sum, o_sq, o_scr;
+    size_t scr_doubles;
+    int chain0;
+};
+
+struct ChainHost {
+    size_t o_rho, o_mu, o_spec, o_tpart, o_acc, o_log, o_prog, o_trace;
+};
+
+}  // namespace
+
+struct bdecon_handle {
+    std::vector<ProbHost> probs;
+    std::vector<ChainHost> chh;
+    std::vector<Image> imgs;
+    std::vector<Chain> chains;
+    int precision = 1;
+    int max_sweeps = 4096;
+    int64_t sweeps = 0;
+    int warps = 1;
+    bool user_warps = false;
+    int grid = 0;
+    bool failed = false;
+    int sms = 0;
+    cudaStream_t st = nullptr;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    bool own_arena = false;
+    size_t o_imgs = 0, o_chains = 0, o_err = 0, o_out = 0, o_scr = 0, o_up = 0;
+    size_t up_bytes = 0;
+    Image* d_imgs = nullptr;
+    Chain* d_chains = nullptr;
+    int* d_err = nullptr;
+    double* d_out = nullptr;        // small read-out buffer
+    double* d_up = nullptr;         // staging buffer for set_state / results
+    int64_t launches = 0;
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;    // pairs (start, stop), reused
+    size_t ev_used = 0;
+    std::string err;
+};
+
+namespace {
+
+bdecon_status fail(bdecon_handle* h, bdecon_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf; else g_err = buf;
+    return s;
+}
+
+#define CK(h, call)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) return fail((h), BDECON_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Alloc {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        off = align_up(off, 256);
+        size_t r = off;
+        off += bytes;
+        return r;
+    }
+};
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+bdecon_status validate(const bdecon_problem& p, int idx)
+{
+    if (p.H < 1 || p.W < 1 || p.H > 16384 || p.W > 16384)
+        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: frame size %dx%d out of range", idx, p.H, p.W);
+    if (!p.image || !p.psf) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: image and psf are required", idx);
+    if (p.L < 1 || p.L > kMaxL || p.L % 2 == 0)
+        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: PSF side %d must be odd and <= %d", idx, p.L, kMaxL);
+    const int S = p.stride ? p.stride : p.L;
+    if (S < p.L || S > kMaxS)
+        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: stride %d must be in [L=%d, %d]", idx, S, p.L, kMaxS);
+    if (p.n_chains < 1 || p.n_chains > 4096) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: n_chains %d", idx, p.n_chains);
+    if (p.precision != BDECON_FP32 && p.precision != BDECON_FP64)
+        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: precision %d", idx, p.precision);
+    if (p.burn_in < 0 || p.refresh_every < 0 || p.max_sweeps < 0)
+        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: negative burn_in/refresh_every/max_sweeps", idx);
+    if (!(p.step >= 0.0) || !std::isfinite(p.step)) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: step", idx);
+    double s = 0.0;
+    for (int k = 0; k < p.L * p.L; ++k) {
+        if (!std::isfinite(p.psf[k]) || p.psf[k] < 0.0)
+            return fail(nullptr, BDECON_ERR_INVALID, "problem %d: PSF entry %d is negative or not finite", idx, k);
+        s += p.psf[k];
+    }
+    if (!(s > 0.0)) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: PSF sums to zero", idx);
+    const int64_t n = (int64_t)p.H * p.W;
+    for (int64_t k = 0; k < n; ++k)
+        if (!std::isfinite(p.image[k])) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: image[%lld] not finite", idx, (long long)k);
+    if (p.gain_map) {
+        for (int64_t k = 0; k < n; ++k)
+            if (!finite_pos(p.gain_map[k])) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: gain_map[%lld] must be > 0", idx, (long long)k);
+    } else if (!finite_pos(p.gain)) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: gain must be > 0", idx);
+    if (p.var_map) {
+        for (int64_t k = 0; k < n; ++k)
+            if (!finite_pos(p.var_map[k])) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: var_map[%lld] must be > 0", idx, (long long)k);
+    } else if (!finite_pos(p.read_var)) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: read_var must be > 0", idx);
+    if (p.offset_map) {
+        for (int64_t k = 0; k < n; ++k)
+            if (!std::isfinite(p.offset_map[k])) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: offset_map not finite", idx);
+    } else if (!std::isfinite(p.offset)) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: offset not finite", idx);
+    return BDECON_OK;
+}
+
+// canonical half of the ph x pw frequencies: (k, l) kept iff it is not larger
+// (lexicographically) than its conjugate partner ((-k) mod ph, (-l) mod pw)
+void half_entries(int ph, int pw, std::vector<int>& out)
+{
+    for (int k = 0; k < ph; ++k)
+        for (int l = 0; l < pw; ++l) {
+            const int kc = (ph - k) % ph, lc = (pw - l) % pw;
+            if (k < kc || (k == kc && l <= lc)) out.push_back((k << 16) | l);
+        }
+}
+
+void describe(ProbHost& ph)
+{
+    const bdecon_problem& p = ph.p;
+    ph.H = p.H; ph.W = p.W; ph.L = p.L; ph.R = p.L / 2;
+    ph.S = p.stride ? p.stride : p.L;
+    ph.Ho = p.H + 2 * ph.R; ph.Wo = p.W + 2 * ph.R;
+    ph.npi = (ph.Ho + ph.S - 1) / ph.S; ph.npj = (ph.Wo + ph.S - 1) / ph.S;
+    ph.n_patches = ph.npi * ph.npj;
+    ph.pitch = (int)align_up((size_t)p.W, 4);
+    const int rh = ph.Ho - (ph.npi - 1) * ph.S, rw = ph.Wo - (ph.npj - 1) * ph.S;   // last patch sides
+    int twoff = 0;
+    ph.ent_kl.clear();
+    for (int s = 0; s < kMaxShapes; ++s) {
+        Shape& sh = ph.shape[s];
+        const bool pr = (s & 2) != 0, pc = (s & 1) != 0;
+        // a shape exists if some patch has it
+        const bool exists = (!pr || rh < ph.S) && (!pc || rw < ph.S);
+        std::memset(&sh, 0, sizeof sh);
+        if (!exists) continue;
+        sh.ph = pr ? rh : ph.S;
+        sh.pw = pc ? rw : ph.S;
+        sh.K = sh.ph * sh.pw;
+        sh.ent_off = (int)ph.ent_kl.size();
+        half_entries(sh.ph, sh.pw, ph.ent_kl);
+        sh.nhalf = (int)ph.ent_kl.size() - sh.ent_off;
+        sh.twh_off = twoff; twoff += sh.ph;
+        sh.tww_off = twoff; twoff += sh.pw;
+    }
+    ph.n_tw = twoff;
+    ph.patch_off.resize(ph.n_patches);
+    int64_t off = 0;
+    for (int pi = 0; pi < ph.npi; ++pi)
+        for (int pj = 0; pj < ph.npj; ++pj) {
+            const int s = (((pi + 1) * ph.S > ph.Ho) ? 2 : 0) | (((pj + 1) * ph.S > ph.Wo) ? 1 : 0);
+            ph.patch_off[pi * ph.npj + pj] = off;
+            off += ph.shape[s].nhalf;
+        }
+    ph.spec_len = off;
+}
+
+int blocks_of(const ProbHost& ph)
+{
+    return ph.p.n_chains * ((ph.npi + ph.tpi - 1) / ph.tpi) * ((ph.npj + ph.tpj - 1) / ph.tpj);
+}
+
+int occupancy(int prec, int warps)
+{
+    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(warps) : sweep_blocks_per_sm<double>(warps);
+}
+
+// automatic plan: one patch per tile and one warp per block while everything
+// fits co-resident; otherwise grow the tiles of the problem with the most
+// blocks until the whole batch fits.
+bdecon_status make_plan(bdecon_handle* h)
+{
+    if (!h->user_warps) h->warps = 1;
+    const int bps = occupancy(h->precision, h->warps);
+    if (bps <= 0) return fail(h, BDECON_ERR_CUDA, "occupancy query failed for %d warps", h->warps);
+    const int cap = bps * h->sms;
+    for (auto& ph : h->probs)
+        if (!ph.user_plan) ph.tpi = ph.tpj = 1;
+    for (;;) {
+        int tot = 0, worst = -1, wb = -1;
+        for (size_t k = 0; k < h->probs.size(); ++k) {
+            const int b = blocks_of(h->probs[k]);
+            tot += b;
+            if (!h->probs[k].user_plan && b > wb) { wb = b; worst = (int)k; }
+        }
+        if (tot <= cap) { h->grid = tot; break; }
+        if (worst < 0) return fail(h, BDECON_ERR_INVALID, "plan needs %d co-resident blocks, at most %d fit", tot, cap);
+        ProbHost& ph = h->probs[worst];
+        if (ph.tpi >= ph.npi && ph.tpj >= ph.npj)
+            return fail(h, BDECON_ERR_INVALID, "batch too large for one co-resident launch (%d blocks, %d fit)", tot, cap);
+        if ((ph.tpj <= ph.tpi && ph.tpj < ph.npj) || ph.tpi >= ph.npi) ++ph.tpj; else ++ph.tpi;
+    }
+    int base = 0;
+    for (size_t k = 0; k < h->probs.size(); ++k) {
+        ProbHost& ph = h->probs[k];
+        const int nti = (ph.npi + ph.tpi - 1) / ph.tpi, ntj = (ph.npj + ph.tpj - 1) / ph.tpj;
+        for (int c = 0; c < ph.p.n_chains; ++c) {
+            Chain& ch = h->chains[ph.chain0 + c];
+            ch.tpi = ph.tpi; ch.tpj = ph.tpj; ch.nti = nti; ch.ntj = ntj;
+            ch.cta_base = base;
+            base += nti * ntj;
+        }
+    }
+    h->grid = base;
+    CK(h, cudaMemcpyAsync(h->d_chains, h->chains.data(), sizeof(Chain) * h->chains.size(), cudaMemcpyHostToDevice, h->st));
+    return BDECON_OK;
+}
+
+size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainHost>& chh, int prec, int max_sweeps)
+{
+    Alloc A;
+    const size_t ts = prec == BDECON_FP32 ? 4 : 8;
+    size_t up = 0;
+    size_t scr_max = 0;
+    chh.clear();
+    for (auto& ph : probs) {
+        const size_t npix = (size_t)ph.H * ph.W, nobj = (size_t)ph.Ho * ph.Wo, nh = ph.ent_kl.size();
+        ph.o_K64 = A.take(8 * ph.L * ph.L);
+        ph.o_K32 = A.take(4 * ph.L * ph.L);
+        ph.o_dat64 = A.take(32 * npix);
+        ph.o_dat32 = A.take(16 * npix);
+        ph.o_ekl = A.take(4 * nh);
+        ph.o_wa64 = A.take(8 * nh);
+        ph.o_m64 = A.take(8 * nh);
+        ph.o_wa32 = A.take(4 * nh);
+        ph.o_m32 = A.take(4 * nh);
+        ph.o_tw64 = A.take(16 * ph.n_tw);
+        ph.o_tw32 = A.take(8 * ph.n_tw);
+        ph.o_poff = A.take(8 * ph.n_patches);
+        ph.o_sum = A.take(8 * nobj * ph.p.n_chains);
+        ph.o_sq = (ph.p.flags & BDECON_FLAG_SECOND_MOMENT) ? A.take(8 * nobj * ph.p.n_chains) : 0;
+        const size_t nblk = (npix + kRedThreads - 1) / kRedThreads;
+        ph.scr_doubles = std::max(nblk + (size_t)ph.n_patches + 8, nblk + 8 + 2 * (size_t)kMaxS * kMaxS) + 8;
+        ph.o_scr = A.take(8 * ph.scr_doubles);
+        scr_max = std::max(scr_max, ph.scr_doubles);
+        up = std::max(up, std::max(16 * npix + 8 * (size_t)ph.L * ph.L, 8 * nobj));
+        ph.chain0 = (int)chh.size();
+        for (int c = 0; c < ph.p.n_chains; ++c) {
+            ChainHost x;
+            x.o_rho = A.take(ts * nobj);
+            x.o_mu = A.take(ts * (size_t)ph.H * ph.pitch);
+            x.o_spec = A.take(2 * ts * (size_t)ph.spec_len);
+            x.o_tpart = A.take(8 * (size_t)kMaxSlots * ph.n_patches);
+            x.o_acc = A.take(8 * (size_t)max_sweeps);
+            x.o_log = (ph.p.flags & BDECON_FLAG_ACCEPT_LOG) ? A.take((size_t)max_sweeps * nobj) : 0;
+            x.o_prog = A.take(4 * (size_t)ph.n_patches);
+            x.o_trace = A.take(8 * ((size_t)max_sweeps + 1));
+            chh.push_back(x);
+        }
+    }
+    h->o_imgs = A.take(sizeof(Image) * probs.size());
+    h->o_chains = A.take(sizeof(Chain) * chh.size());
+    h->o_err = A.take(64);
+    h->o_out = A.take(64);
+    h->up_bytes = up;
+    h->o_up = A.take(up);
+    (void)scr_max;
+    return align_up(A.off, 256);
+}
+
+template <typename T>
+bdecon_status refresh_chain(bdecon_handle* h, int ci, int write, double* out)
+{
+    const Chain& ch = h->chains[ci];
+    const ProbHost& ph = h->probs[ch.img];
+    launch_refresh<T>(h->imgs[ch.img], ch, (double*)(h->arena + ph.o_scr), write, out, h->d_err, h->st, &h->launches);
+    CK(h, cudaGetLastError());
+    return BDECON_OK;
+}
+
+bdecon_status refresh(bdecon_handle* h, int ci, int write, double* out)
+{
+    return h->precision == BDECON_FP32 ? refresh_chain<float>(h, ci, write, out) : refresh_chain<double>(h, ci, write, out);
+}
+
+bdecon_status check_device(bdecon_handle* h)
+{
+    int e = 0;
+    CK(h, cudaStreamSynchronize(h->st));
+    CK(h, cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e & kErrTimeout) { h->failed = true; return fail(h, BDECON_ERR_TIMEOUT, "a sub-lattice wait timed out on the device"); }
+    if (e & kErrNumeric) { h->failed = true; return fail(h, BDECON_ERR_NUMERIC, "non-finite or non-positive expected image"); }
+    return BDECON_OK;
+}
+
+bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* ws, size_t ws_bytes, bdecon_handle** out)
+{
+    if (!out) return fail(nullptr, BDECON_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!ps || n < 1) return fail(nullptr, BDECON_ERR_INVALID, "no problems");
+    for (int k = 0; k < n; ++k) {
+        bdecon_status s = validate(ps[k], k);
+        if (s != BDECON_OK) return s;
+        if (ps[k].precision != ps[0].precision)
+            return fail(nullptr, BDECON_ERR_INVALID, "all problems of a batch must use the same precision");
+    }
+    bdecon_handle* h = new bdecon_handle();
+    h->precision = ps[0].precision;
+    h->st = (cudaStream_t)stream;
+    h->max_sweeps = 0;
+    for (int k = 0; k < n; ++k) h->max_sweeps = std::max(h->max_sweeps, ps[k].max_sweeps ? ps[k].max_sweeps : 4096);
+    h->probs.resize(n);
+    for (int k = 0; k < n; ++k) {
+        h->probs[k].p = ps[k];
+        if (h->probs[k].p.step == 0.0) h->probs[k].p.step = 0.2;
+        describe(h->probs[k]);
+    }
+    int dev = 0;
+    auto bail = [&](bdecon_status s) {
+        std::string m = h->err;
+        if (h->own_arena && h->arena) cudaFree(h->arena);
+        delete h;
+        g_err = m;
+        return s;
+    };
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(fail(h, BDECON_ERR_CUDA, "no CUDA device"));
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return bail(fail(h, BDECON_ERR_CUDA, "device does not support cooperative launches"));
+    const size_t need = layout(h, h->probs, h->chh, h->precision, h->max_sweeps);
+    if (ws) {
+        if (ws_bytes < need) return bail(fail(h, BDECON_ERR_NOMEM, "workspace of %zu bytes, %zu needed", ws_bytes, need));
+        if (((uintptr_t)ws) % 256) return bail(fail(h, BDECON_ERR_INVALID, "workspace must be 256-byte aligned"));
+        h->arena = (char*)ws;
+        h->own_arena = false;
+    } else {
+        void* p = nullptr;
+        if (cudaMalloc(&p, need) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(h, BDECON_ERR_NOMEM, "cudaMalloc of %zu bytes failed", need));
+        }
+        h->arena = (char*)p;
+        h->own_arena = true;
+    }
+    h->arena_bytes = need;
+    if (cudaMemsetAsync(h->arena, 0, need, h->st) != cudaSuccess) return bail(fail(h, BDECON_ERR_CUDA, "memset"));
+    h->d_imgs = (Image*)(h->arena + h->o_imgs);
+    h->d_chains = (Chain*)(h->arena + h->o_chains);
+    h->d_err = (int*)(h->arena + h->o_err);
+    h->d_out = (double*)(h->arena + h->o_out);
+    h->d_up = (double*)(h->arena + h->o_up);
+    // descriptors
+    h->imgs.resize(n);
+    for (int k = 0; k < n; ++k) {
+        ProbHost& ph = h->probs[k];
+        Image& im = h->imgs[k];
+        std::memset(&im, 0, sizeof im);
+        im.H = ph.H; im.W = ph.W; im.L = ph.L; im.R = ph.R; im.S = ph.S; im.Ho = ph.Ho; im.Wo = ph.Wo;
+        im.npi = ph.npi; im.npj = ph.npj; im.mu_pitch = ph.pitch; im.n_chains = ph.p.n_chains;
+        im.seed_lo = (uint32_t)(ph.p.seed & 0xffffffffu); im.seed_hi = (uint32_t)(ph.p.seed >> 32);
+        im.step = ph.p.step; im.burn_in = ph.p.burn_in; im.refresh_every = ph.p.refresh_every;
+        im.n_patches = ph.n_patches; im.chain0 = ph.chain0;
+        char* A = h->arena;
+        im.K64 = (const double*)(A + ph.o_K64); im.K32 = (const float*)(A + ph.o_K32);
+        im.dat64 = (const double*)(A + ph.o_dat64); im.dat32 = (const float*)(A + ph.o_dat32);
+        for (int s = 0; s < kMaxShapes; ++s) im.shape[s] = ph.shape[s];
+        im.ent_kl = (const int*)(A + ph.o_ekl);
+        im.ent_wa64 = (const double*)(A + ph.o_wa64); im.ent_m64 = (const double*)(A + ph.o_m64);
+        im.ent_wa32 = (const float*)(A + ph.o_wa32); im.ent_m32 = (const float*)(A + ph.o_m32);
+        im.tw64 = (const double*)(A + ph.o_tw64); im.tw32 = (const float*)(A + ph.o_tw32);
+        im.patch_off = (const int64_t*)(A + ph.o_poff);
+        im.spec_len = ph.spec_len;
+    }
+    h->chains.resize(h->chh.size());
+    for (int k = 0; k < n; ++k) {
+        ProbHost& ph = h->probs[k];
+        for (int c = 0; c < ph.p.n_chains; ++c) {
+            const ChainHost& x = h->chh[ph.chain0 + c];
+            Chain& ch = h->chains[ph.chain0 + c];
+            std::memset(&ch, 0, sizeof ch);
+            char* A = h->arena;
+            const size_t nobj = (size_t)ph.Ho * ph.Wo;
+            ch.img = k; ch.chain = c;
+            ch.rho = A + x.o_rho; ch.mu = A + x.o_mu; ch.spec = A + x.o_spec;
+            ch.rho_sum = (double*)(A + ph.o_sum) + c * nobj;
+            ch.rho_sq = ph.o_sq ? (double*)(A + ph.o_sq) + c * nobj : nullptr;
+            ch.trace_part = (double*)(A + x.o_tpart);
+            ch.acc_count = (unsigned long long*)(A + x.o_acc);
+            ch.acc_log = x.o_log ? (uint8_t*)(A + x.o_log) : nullptr;
+            ch.prog = (int*)(A + x.o_prog);
+            ch.trace = (double*)(A + x.o_trace);
+        }
+    }
+    if (cudaMemcpyAsync(h->d_imgs, h->imgs.data(), sizeof(Image) * n, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+        return bail(fail(h, BDECON_ERR_CUDA, "descriptor upload"));
+    // static tables (host-side index bookkeeping only)
+    for (int k = 0; k < n; ++k) {
+        ProbHost& ph = h->probs[k];
+        if (cudaMemcpyAsync(h->arena + ph.o_ekl, ph.ent_kl.data(), 4 * ph.ent_kl.size(), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
+            cudaMemcpyAsync(h->arena + ph.o_poff, ph.patch_off.data(), 8 * ph.patch_off.size(), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            return bail(fail(h, BDECON_ERR_CUDA, "table upload"));
+    }
+    // per problem: upload inputs (host -> device), set-up kernels, initial objects, refresh
+    for (int k = 0; k < n; ++k) {
+        ProbHost& ph = h->probs[k];
+        const bdecon_problem& p = ph.p;
+        const size_t npix = (size_t)ph.H * ph.W;
+        float* u_w = (float*)h->d_up;
+        float* u_g = u_w + npix;
+        float* u_o = u_g + npix;
+        float* u_v = u_o + npix;
+        double* u_psf = (double*)(u_v + npix);
+        cudaError_t e = cudaMemcpyAsync(u_w, p.image, 4 * npix, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess && p.gain_map) e = cudaMemcpyAsync(u_g, p.gain_map, 4 * npix, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess && p.offset_map) e = cudaMemcpyAsync(u_o, p.offset_map, 4 * npix, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess && p.var_map) e = cudaMemcpyAsync(u_v, p.var_map, 4 * npix, cudaMemcpyHostToDevice, h->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u_psf, p.psf, 8 * (size_t)ph.L * ph.L, cudaMemcpyHostToDevice, h->st);
+        if (e != cudaSuccess) return bail(fail(h, BDECON_ERR_CUDA, "input upload: %s", cudaGetErrorString(e)));
+        double* scr = (double*)(h->arena + ph.o_scr);
+        double* b0 = h->d_out;
+        launch_setup(h->imgs[k], h->d_imgs + k, u_w, p.gain_map ? u_g : nullptr, p.offset_map ? u_o : nullptr,
+                     p.var_map ? u_v : nullptr, p.gain, p.offset, p.read_var, u_psf, b0, scr, h->st, &h->launches);
+        for (int c = 0; c < p.n_chains; ++c) {
+            const Chain& ch = h->chains[ph.chain0 + c];
+            if (h->precision == BDECON_FP32) launch_init_rho<float>(h->imgs[k], ch, b0, h->st, &h->launches);
+            else launch_init_rho<double>(h->imgs[k], ch, b0, h->st, &h->launches);
+        }
+        // the staging buffer is reused by the next problem: finish this one first
+        if (cudaStreamSynchronize(h->st) != cudaSuccess) return bail(fail(h, BDECON_ERR_CUDA, "set-up: %s", cudaGetErrorString(cudaGetLastError())));
+        for (int c = 0; c < p.n_chains; ++c) {
+            const Chain& ch = h->chains[ph.chain0 + c];
+            if (refresh(h, ph.chain0 + c, 1, ch.trace) != BDECON_OK) return bail(BDECON_ERR_CUDA);
+        }
+    }
+    bdecon_status s = make_plan(h);
+    if (s != BDECON_OK) return bail(s);
+    s = check_device(h);
+    if (s != BDECON_OK) return bail(s);
+    *out = h;
+    return BDECON_OK;
+}
+
+bdecon_status chain_index(bdecon_handle* h, int p, int c, int* ci)
+{
+    if (p < 0 || p >= (int)h->probs.size()) return fail(h, BDECON_ERR_INVALID, "problem index %d", p);
+    if (c < 0 || c >= h->probs[p].p.n_chains) return fail(h, BDECON_ERR_INVALID, "chain index %d", c);
+    *ci = h->probs[p].chain0 + c;
+    return BDECON_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+bdecon_status bdecon_workspace_size(const bdecon_problem* ps, int32_t n, size_t* bytes)
+{
+    if (!ps || n < 1 || !bytes) return fail(nullptr, BDECON_ERR_INVALID, "bad arguments");
+    for (int k = 0; k < n; ++k) {
+        bdecon_status s = validate(ps[k], k);
+        if (s != BDECON_OK) return s;
+    }
+    bdecon_handle tmp;
+    std::vector<ProbHost> probs(n);
+    int ms = 0;
+    for (int k = 0; k < n; ++k) {
+        probs[k].p = ps[k];
+        describe(probs[k]);
+        ms = std::max(ms, ps[k].max_sweeps ? ps[k].max_sweeps : 4096);
+    }
+    std::vector<ChainHost> chh;
+    *bytes = layout(&tmp, probs, chh, ps[0].precision, ms);
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_create(const bdecon_problem* p, void* stream, bdecon_handle** out)
+{
+    return create_impl(p, 1, stream, nullptr, 0, out);
+}
+
+bdecon_status bdecon_batch_create(const bdecon_problem* ps, int32_t n, void* stream, bdecon_handle** out)
+{
+    return create_impl(ps, n, stream, nullptr, 0, out);
+}
+
+bdecon_status bdecon_create_in(const bdecon_problem* ps, int32_t n, void* stream, void* ws, size_t bytes,
+                               bdecon_handle** out)
+{
+    if (!ws) return fail(nullptr, BDECON_ERR_INVALID, "workspace is NULL");
+    return create_impl(ps, n, stream, ws, bytes, out);
+}
+
+void bdecon_destroy(bdecon_handle* h)
+{
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+    for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+    if (h->own_arena && h->arena) cudaFree(h->arena);
+    delete h;
+}
+
+const char* bdecon_last_error(const bdecon_handle* h)
+{
+    return h ? h->err.c_str() : g_err.c_str();
+}
+
+bdecon_status bdecon_sweep(bdecon_handle* h, int32_t n)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    if (h->failed) return fail(h, BDECON_ERR_STATE, "handle failed earlier: %s", h->err.c_str());
+    if (n < 0) return fail(h, BDECON_ERR_INVALID, "negative sweep count");
+    if (h->sweeps + n > h->max_sweeps)
+        return fail(h, BDECON_ERR_INVALID, "trace capacity %d exceeded (%lld + %d sweeps)", h->max_sweeps,
+                    (long long)h->sweeps, n);
+    while (n > 0) {
+        const int t0 = (int)h->sweeps;
+        int len = std::min(n, kMaxSlots);
+        for (auto& ph : h->probs)
+            if (ph.p.refresh_every > 0) len = std::min(len, (t0 / ph.p.refresh_every + 1) * ph.p.refresh_every - t0);
+        for (size_t ci = 0; ci < h->chains.size(); ++ci) {
+            const Chain& ch = h->chains[ci];
+            const ProbHost& ph = h->probs[ch.img];
+            CK(h, cudaMemsetAsync(ch.trace_part, 0, 8 * (size_t)len * ph.n_patches, h->st));
+            CK(h, cudaMemsetAsync(ch.prog, 0, 4 * (size_t)ph.n_patches, h->st));
+        }
+        SweepArgs a;
+        a.imgs = h->d_imgs; a.chains = h->d_chains; a.n_chains = (int)h->chains.size();
+        a.t0 = t0; a.n_sweeps = len; a.err = h->d_err;
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (h->timing) {
+            if (h->ev_used + 2 > h->ev_pool.size()) {
+                for (int k = 0; k < 2; ++k) {
+                    cudaEvent_t ev;
+                    CK(h, cudaEventCreate(&ev));
+                    h->ev_pool.push_back(ev);
+                }
+            }
+            ev0 = h->ev_pool[h->ev_used];
+            ev1 = h->ev_pool[h->ev_used + 1];
+            h->ev_used += 2;
+            CK(h, cudaEventRecord(ev0, h->st));
+        }
+        cudaError_t e = h->precision == BDECON_FP32 ? launch_sweep<float>(a, h->grid, h->warps, h->st)
+                                                    : launch_sweep<double>(a, h->grid, h->warps, h->st);
+        if (h->timing) CK(h, cudaEventRecord(ev1, h->st));
+        if (e != cudaSuccess) return fail(h, BDECON_ERR_CUDA, "sweep launch (%d blocks x %d warps): %s", h->grid, h->warps, cudaGetErrorString(e));
+        ++h->launches;
+        launch_trace(h->d_imgs, h->d_chains, (int)h->chains.size(), t0, len, h->st, &h->launches);
+        CK(h, cudaGetLastError());
+        h->sweeps += len;
+        n -= len;
+        for (auto& ph : h->probs) {
+            for (int t = t0 + 1; t <= t0 + len; ++t)
+                if (t > ph.p.burn_in) ++ph.n_sum;
+            if (ph.p.refresh_every > 0 && h->sweeps % ph.p.refresh_every == 0)
+                for (int c = 0; c < ph.p.n_chains; ++c) {
+                    const int ci = ph.chain0 + c;
+                    bdecon_status s = refresh(h, ci, 1, h->chains[ci].trace + h->sweeps);
+                    if (s != BDECON_OK) return s;
+                }
+        }
+    }
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_sync(bdecon_handle* h)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    return check_device(h);
+}
+
+bdecon_status bdecon_posterior_mean(bdecon_handle* h, int32_t p, double* out, int32_t crop)
+{
+    if (!h || !out) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, 0, &ci);
+    if (s != BDECON_OK) return s;
+    ProbHost& ph = h->probs[p];
+    if (ph.n_sum == 0) return fail(h, BDECON_ERR_STATE, "no sweep after burn-in yet");
+    const int oh = crop ? ph.H : ph.Ho, ow = crop ? ph.W : ph.Wo;
+    launch_mean(h->chains[ci].rho_sum, ph.p.n_chains, (int64_t)ph.Ho * ph.Wo, ph.Ho, ph.Wo, crop ? ph.R : 0, oh, ow,
+                1.0 / ((double)ph.n_sum * ph.p.n_chains), h->d_up, nullptr, 0, h->st, &h->launches);
+    CK(h, cudaMemcpyAsync(out, h->d_up, 8 * (size_t)oh * ow, cudaMemcpyDeviceToHost, h->st));
+    return check_device(h);
+}
+
+bdecon_status bdecon_posterior_var(bdecon_handle* h, int32_t p, double* out, int32_t crop)
+{
+    if (!h || !out) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, 0, &ci);
+    if (s != BDECON_OK) return s;
+    ProbHost& ph = h->probs[p];
+    if (!ph.o_sq) return fail(h, BDECON_ERR_STATE, "created without BDECON_FLAG_SECOND_MOMENT");
+    if (ph.n_sum == 0) return fail(h, BDECON_ERR_STATE, "no sweep after burn-in yet");
+    const int oh = crop ? ph.H : ph.Ho, ow = crop ? ph.W : ph.Wo;
+    launch_mean(h->chains[ci].rho_sum, ph.p.n_chains, (int64_t)ph.Ho * ph.Wo, ph.Ho, ph.Wo, crop ? ph.R : 0, oh, ow,
+                1.0 / ((double)ph.n_sum * ph.p.n_chains), h->d_up, h->chains[ci].rho_sq, 1, h->st, &h->launches);
+    CK(h, cudaMemcpyAsync(out, h->d_up, 8 * (size_t)oh * ow, cudaMemcpyDeviceToHost, h->st));
+    return check_device(h);
+}
+
+bdecon_status bdecon_log_posterior_trace(bdecon_handle* h, int32_t p, int32_t c, double* out, size_t cap, size_t* n)
+{
+    if (!h || !n) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    *n = (size_t)h->sweeps;
+    if (out && cap) {
+        const size_t k = std::min(cap, (size_t)h->sweeps);
+        CK(h, cudaMemcpyAsync(out, h->chains[ci].trace + 1, 8 * k, cudaMemcpyDeviceToHost, h->st));
+    }
+    return check_device(h);
+}
+
+bdecon_status bdecon_accept_counts(bdecon_handle* h, int32_t p, int32_t c, int64_t* out, size_t cap, size_t* n)
+{
+    if (!h || !n) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    *n = (size_t)h->sweeps;
+    if (out && cap) {
+        const size_t k = std::min(cap, (size_t)h->sweeps);
+        CK(h, cudaMemcpyAsync(out, h->chains[ci].acc_count, 8 * k, cudaMemcpyDeviceToHost, h->st));
+    }
+    return check_device(h);
+}
+
+bdecon_status bdecon_accept_log(bdecon_handle* h, int32_t p, int32_t c, uint8_t* out, size_t cap, size_t* n)
+{
+    if (!h || !n) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    if (!h->chains[ci].acc_log) return fail(h, BDECON_ERR_STATE, "created without BDECON_FLAG_ACCEPT_LOG");
+    const ProbHost& ph = h->probs[p];
+    *n = (size_t)h->sweeps * ph.Ho * ph.Wo;
+    if (out && cap) CK(h, cudaMemcpyAsync(out, h->chains[ci].acc_log, std::min(cap, *n), cudaMemcpyDeviceToHost, h->st));
+    return check_device(h);
+}
+
+bdecon_status bdecon_get_state(bdecon_handle* h, int32_t p, int32_t c, double* rho, int64_t* sweeps)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    const ProbHost& ph = h->probs[p];
+    if (sweeps) *sweeps = h->sweeps;
+    if (rho) {
+        const int64_t n = (int64_t)ph.Ho * ph.Wo;
+        if (h->precision == BDECON_FP32) launch_convert<float>(h->chains[ci].rho, h->d_up, n, ph.Ho, ph.Wo, ph.Wo, h->st, &h->launches);
+        else launch_convert<double>(h->chains[ci].rho, h->d_up, n, ph.Ho, ph.Wo, ph.Wo, h->st, &h->launches);
+        CK(h, cudaMemcpyAsync(rho, h->d_up, 8 * (size_t)n, cudaMemcpyDeviceToHost, h->st));
+    }
+    return check_device(h);
+}
+
+bdecon_status bdecon_get_mu(bdecon_handle* h, int32_t p, int32_t c, double* mu)
+{
+    if (!h || !mu) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    const ProbHost& ph = h->probs[p];
+    const int64_t n = (int64_t)ph.H * ph.W;
+    if (h->precision == BDECON_FP32) launch_convert<float>(h->chains[ci].mu, h->d_up, n, ph.H, ph.W, ph.pitch, h->st, &h->launches);
+    else launch_convert<double>(h->chains[ci].mu, h->d_up, n, ph.H, ph.W, ph.pitch, h->st, &h->launches);
+    CK(h, cudaMemcpyAsync(mu, h->d_up, 8 * (size_t)n, cudaMemcpyDeviceToHost, h->st));
+    return check_device(h);
+}
+
+bdecon_status bdecon_set_state(bdecon_handle* h, int32_t p, int32_t c, const double* rho, int64_t sweeps)
+{
+    if (!h || !rho) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    if (sweeps < 0 || sweeps > h->max_sweeps) return fail(h, BDECON_ERR_INVALID, "sweep counter %lld out of range", (long long)sweeps);
+    const ProbHost& ph0 = h->probs[p];
+    const int64_t n = (int64_t)ph0.Ho * ph0.Wo;
+    for (int64_t k = 0; k < n; ++k)
+        if (!(std::isfinite(rho[k]) && rho[k] > 0.0)) return fail(h, BDECON_ERR_INVALID, "rho[%lld] must be finite and > 0", (long long)k);
+    s = check_device(h);
+    if (s != BDECON_OK) return s;
+    CK(h, cudaMemcpyAsync(h->d_up, rho, 8 * (size_t)n, cudaMemcpyHostToDevice, h->st));
+    if (h->precision == BDECON_FP32) launch_set_rho<float>(h->d_up, h->chains[ci].rho, n, h->st, &h->launches);
+    else launch_set_rho<double>(h->d_up, h->chains[ci].rho, n, h->st, &h->launches);
+    h->sweeps = sweeps;
+    // the sweep counter is shared by every chain of the handle: rebase all traces
+    for (size_t k = 0; k < h->chains.size(); ++k) {
+        s = refresh(h, (int)k, 1, h->chains[k].trace + sweeps);
+        if (s != BDECON_OK) return s;
+    }
+    for (auto& ph : h->probs) {
+        ph.n_sum = 0;
+        for (int k = 0; k < ph.p.n_chains; ++k) {
+            const Chain& ch = h->chains[ph.chain0 + k];
+            CK(h, cudaMemsetAsync(ch.rho_sum, 0, 8 * (size_t)ph.Ho * ph.Wo, h->st));
+            if (ch.rho_sq) CK(h, cudaMemsetAsync(ch.rho_sq, 0, 8 * (size_t)ph.Ho * ph.Wo, h->st));
+        }
+    }
+    return check_device(h);
+}
+
+bdecon_status bdecon_log_posterior(bdecon_handle* h, int32_t p, int32_t c, double* out)
+{
+    if (!h || !out) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    s = refresh(h, ci, 0, h->d_out);
+    if (s != BDECON_OK) return s;
+    CK(h, cudaMemcpyAsync(out, h->d_out, 8, cudaMemcpyDeviceToHost, h->st));
+    return check_device(h);
+}
+
+bdecon_status bdecon_delta(bdecon_handle* h, int32_t p, int32_t c, int64_t m, double rho_new, double* dL, double* dP,
+                           int32_t* ok)
+{
+    if (!h || !dL || !dP || !ok) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    const ProbHost& ph = h->probs[p];
+    if (m < 0 || m >= (int64_t)ph.Ho * ph.Wo) return fail(h, BDECON_ERR_INVALID, "pixel %lld out of range", (long long)m);
+    if (!(std::isfinite(rho_new) && rho_new > 0.0)) return fail(h, BDECON_ERR_INVALID, "rho_new must be finite and > 0");
+    if (h->precision == BDECON_FP32) launch_delta<float>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, h->st, &h->launches);
+    else launch_delta<double>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, h->st, &h->launches);
+    CK(h, cudaGetLastError());
+    double r[3];
+    CK(h, cudaMemcpyAsync(r, h->d_out, sizeof r, cudaMemcpyDeviceToHost, h->st));
+    s = check_device(h);
+    if (s != BDECON_OK) return s;
+    *dL = r[0]; *dP = r[1]; *ok = r[2] != 0.0;
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_set_plan(bdecon_handle* h, int32_t p, int32_t tile_i, int32_t tile_j, int32_t warps)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    if (p < 0 || p >= (int)h->probs.size()) return fail(h, BDECON_ERR_INVALID, "problem index %d", p);
+    ProbHost& ph = h->probs[p];
+    const int old_i = ph.tpi, old_j = ph.tpj, old_w = h->warps;
+    const bool old_u = ph.user_plan, old_uw = h->user_warps;
+    if (tile_i == 0) {
+        ph.user_plan = false;
+        h->user_warps = false;
+    } else {
+        if (tile_i < 1 || tile_j < 1 || warps < 1 || warps > 8) return fail(h, BDECON_ERR_INVALID, "bad plan");
+        ph.user_plan = true;
+        ph.tpi = std::min(tile_i, ph.npi);
+        ph.tpj = std::min(tile_j, ph.npj);
+        h->warps = warps;
+        h->user_warps = true;
+    }
+    bdecon_status s = check_device(h);
+    if (s == BDECON_OK) s = make_plan(h);
+    if (s != BDECON_OK) {
+        ph.tpi = old_i; ph.tpj = old_j; h->warps = old_w; ph.user_plan = old_u; h->user_warps = old_uw;
+        std::string m = h->err;
+        make_plan(h);
+        h->err = m;
+    }
+    return s;
+}
+
+bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int32_t* warps, int32_t* tile_i,
+                              int32_t* tile_j)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    if (p < 0 || p >= (int)h->probs.size()) return fail(h, BDECON_ERR_INVALID, "problem index %d", p);
+    if (blocks) *blocks = h->grid;
+    if (warps) *warps = h->warps;
+    if (tile_i) *tile_i = h->probs[p].tpi;
+    if (tile_j) *tile_j = h->probs[p].tpj;
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_launch_count(const bdecon_handle* h, int64_t* launches)
+{
+    if (!h || !launches) return fail(nullptr, BDECON_ERR_INVALID, "bad arguments");
+    *launches = h->launches;
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_set_timing(bdecon_handle* h, int32_t enable)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    h->timing = enable != 0;
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_sweep_kernel_time(bdecon_handle* h, double* ms, int64_t* launches)
+{
+    if (!h || !ms || !launches) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    CK(h, cudaStreamSynchronize(h->st));
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+        float t = 0.f;
+        CK(h, cudaEventElapsedTime(&t, h->ev_pool[k], h->ev_pool[k + 1]));
+        tot += t;
+    }
+    *ms = tot;
+    *launches = (int64_t)(h->ev_used / 2);
+    h->ev_used = 0;
+    return BDECON_OK;
+}
+
+}  // extern "C"

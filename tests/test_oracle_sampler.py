@@ -167,3 +167,21 @@ def test_trace_is_log_posterior_of_state():
     r = orc.run(3, want_samples=True)
     for t in range(3):
         assert r["trace"][t] == orc.log_posterior(r["samples"][t])
+
+
+def test_single_update_matches_first_class_of_a_sweep():
+    # the local evaluation reproduces the chain's first-class decisions
+    prob = synth.small_problem(H=15, W=17, L=5, maps=True, seed=13)
+    orc = O.Oracle(prob)
+    rho0 = orc.init()
+    r = orc.run(1, want_acc_log=True, want_samples=True)
+    S = prob.S
+    Ho, Wo = prob.object_shape()
+    for i in range(0, Ho, S):
+        for j in range(0, Wo, S):
+            m = i * Wo + j
+            acc, rn, dl, dp = orc.single_update(rho0, m, 1)
+            ok, dl2, dp2 = orc.delta(rho0, m, rn)
+            assert acc == bool(r["acc_log"][0, i, j])
+            assert r["samples"][0, i, j] == (rn if acc else rho0[i, j])
+            assert dl == pytest.approx(dl2, abs=1e-10) and dp == pytest.approx(dp2, abs=1e-10)
