@@ -367,6 +367,25 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile(args):
+    """Small case for ncu: the same frame and plan, one warm-up launch and then
+    one sweep-kernel launch of --profile sweeps (no refresh inside it)."""
+    import torch
+    from paper_2411_00991_gb300 import bdecon
+    prob = synth.widefield_512()
+    prob.burn_in = 0
+    prob.refresh_every = 0
+    prec = bdecon.BDECON_FP64 if args.profile_fp64 else bdecon.BDECON_FP32
+    s = bdecon.Sampler(prob, precision=prec, max_sweeps=args.profile + 8,
+                       stream=torch.cuda.current_stream().cuda_stream)
+    s.sweep(2)
+    s.sync()
+    s.sweep(args.profile)
+    s.sync()
+    print(json.dumps({"profile_sweeps": args.profile, "plan": s.get_plan(), "trace_last": float(s.trace()[-1])}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,7 +395,12 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--fp64-sweeps", type=int, default=20)
+    ap.add_argument("--profile", type=int, default=0, help="ncu mode: one launch of this many sweeps")
+    ap.add_argument("--profile-fp64", action="store_true")
     args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

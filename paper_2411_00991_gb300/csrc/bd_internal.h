@@ -50,6 +50,7 @@ struct Image {
     const float* tw32;
     const int64_t* patch_off;        // offset (complex elements) of each patch's half spectrum
     int64_t spec_len;                // complex elements per chain
+    int n_ent, n_tw, max_nhalf;      // table sizes (all shapes)
 };
 
 // One chain (an instance of a problem with its own state and random stream).
@@ -76,7 +77,49 @@ struct SweepArgs {
     int t0;                          // sweeps completed before this launch
     int n_sweeps;                    // sweeps in this launch
     int* err;
+    int resident;                    // 1: tile state (data, spectra, rho) held in shared memory
 };
+
+// Threads that cooperate on one pixel update: a function of the PSF side
+// only, so each update's arithmetic and reduction order never depend on the
+// launch plan.  One warp per 100 window pixels, 1..8 warps (at most 4
+// window pixels per thread up to L = 32).
+__host__ __device__ inline int team_threads(int L)
+{
+    int w = (L * L + 99) / 100;
+    w = w < 1 ? 1 : (w > 8 ? 8 : w);
+    return 32 * w;
+}
+
+// Dynamic shared memory of one sweep block: fixed tables, reduction scratch
+// and (resident plans) the tile's data constants with PSF halo, its patch
+// spectra and its object values.
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+struct SmemPlan {
+    size_t red, K, tw, ekl, ewa, em, spec, rho, dat, total;
+};
+__host__ __device__ inline SmemPlan smem_plan(int L, int S, int n_tw, int n_ent, int max_nhalf, int tpi, int tpj,
+                                              int resident, int tsize)
+{
+    SmemPlan p;
+    size_t o = 0;
+    p.red = o; o += al16((size_t)2 * 8 * 8 * 4 * tsize);
+    p.K = o; o += al16((size_t)L * L * tsize);
+    p.tw = o; o += al16((size_t)2 * n_tw * tsize);
+    p.ekl = o; o += al16((size_t)4 * n_ent);
+    p.ewa = o; o += al16((size_t)n_ent * tsize);
+    p.em = o; o += al16((size_t)n_ent * tsize);
+    if (resident) {
+        const int R = L / 2;
+        p.spec = o; o += al16((size_t)tpi * tpj * max_nhalf * 2 * tsize);
+        p.rho = o; o += al16((size_t)tpi * tpj * S * S * tsize);
+        p.dat = o; o += al16((size_t)(tpi * S + 2 * R) * (tpj * S + 2 * R) * 4 * tsize);
+    } else {
+        p.spec = p.rho = p.dat = o;
+    }
+    p.total = o;
+    return p;
+}
 
 // host launchers (defined in the .cu files)
 void launch_setup(const Image& im, const Image* d_im, const float* w, const float* g,
@@ -90,13 +133,13 @@ template <typename T>
 void launch_refresh(const Image& im, const Chain& ch, double* scratch, int write_state,
                     double* out_logpost, int* err, cudaStream_t st, int64_t* launches);
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs& a, int grid, int warps, cudaStream_t st);
+cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 template <typename T>
-int sweep_blocks_per_sm(int warps);
+int sweep_blocks_per_sm(int threads, size_t smem);
 void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int t0, int n_sweeps,
                   cudaStream_t st, int64_t* launches);
 template <typename T>
-void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3,
+void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3, int L,
                   cudaStream_t st, int64_t* launches);
 template <typename T>
 void launch_convert(const void* src, double* dst, int64_t n, int rows, int cols, int src_pitch,

@@ -11,145 +11,67 @@
 // have finished step s, so every update sees exactly the state the
 // sequential raster scan would give it; there is no grid-wide barrier.
 //
-// Per update (one warp, fixed lane assignment => bit-identical results for
-// any tiling):
+// Each update is done by a team of team_threads(L) threads with a fixed
+// assignment of window pixels and spectrum entries and a fixed reduction
+// tree, so results are bit-identical for every launch plan:
 //   a2  Philox4x32-10 counter (m, t, chain, 0) -> z, u; rho' = rho e^{step z}
-//   a3  dL = sum over the L x L PSF window of the Eq. 6 change (dl_pixel)
-//   a4  dP = patch Dirichlet change (Eq. 7-8) with X'_k = X_k + delta w_k
+//   a4  dP = patch Dirichlet change (Eq. 7-8) with X'_k = X_k + delta w_k,
+//       computed before waiting for the neighbours (it needs only the tile's
+//       own spectrum)
+//   a3  dL = sum over the L x L PSF window of the Eq. 6 change (dl_pixel),
+//       the window's expected-image values fetched in one batch
 //   a5  accept iff log u < dL + dP + step z; write rho, mu window, spectrum
 //   a7  after the last class of a sweep: running sums of rho (double)
-#include <cstdio>
-
+// In a resident plan the tile's per-pixel data constants (with the PSF halo),
+// patch spectra and object values stay in shared memory for the launch; only
+// mu, shared with the neighbouring tiles, is read from global memory (L2).
 #include "bd_device.cuh"
 
 namespace bd {
 
+// One entry of the patch prior change: X' = X + delta w, with
+//   |X'|^2 - |X|^2 = delta (2 Re(X conj w) + delta)        (|w| = 1)
+// accumulates  wa log(|X'|^2/|X|^2),  mult (|X'| - |X|),  mult |X|.
 template <typename T>
-__device__ __forceinline__ void update_pixel(const Image& im, const Chain& ch, int pi, int pj,
-                                             int u, int v, int t, int slot, int& n_acc)
+__device__ __forceinline__ void prior_term(T xr, T xi, T wr, T wi, T delta, T wa, T mult, T& accP, T& accS,
+                                           T& accA, bool& bad)
 {
     using P = Prec<T>;
-    using T2 = typename Vec2<T>::type;
-    const int lane = threadIdx.x & 31;
-    const int sidx = shape_index(im, pi, pj);
-    const Shape& sh = im.shape[sidx];
-    if (u >= sh.ph || v >= sh.pw) return;   // this class has no pixel in a short patch
-    const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W;
-    const int i = pi * S + u, j = pj * S + v;
-    const int m = i * im.Wo + j;
-    const int p = pi * im.npj + pj;
-
-    // a2: proposal
-    const uint4 x = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)t, (uint32_t)ch.chain, 0u),
-                                  im.seed_lo, im.seed_hi);
-    const T z = P::gauss(uniform23<T>(x.x), uniform23<T>(x.y));
-    const T lu = P::log(uniform23<T>(x.z));
-    T* rho = reinterpret_cast<T*>(ch.rho);
-    const T r_old = rho[m];
-    const T step = (T)im.step;
-    const T r_new = r_old * P::exp(step * z);
-    const T delta = r_new - r_old;
-
-    // a3: likelihood change over the PSF window (camera rows i-2R..i, cols j-2R..j)
-    const T* K = kern<T>(im);
-    const Dat4<T>* dt = dat<T>(im);
-    T* mu = reinterpret_cast<T*>(ch.mu);
-    const int a0 = i - 2 * R, b0 = j - 2 * R, LL = L * L;
-    const int sdy = 32 / L, sdx = 32 - sdy * L;
-    bool bad = false;
-    T accL = (T)0;
-    {
-        int dy = lane / L, dx = lane - (lane / L) * L;
-        for (int k = lane; k < LL; k += 32) {
-            const int a = a0 + dy, b = b0 + dx;
-            if ((unsigned)a < (unsigned)H && (unsigned)b < (unsigned)W) {
-                const T xk = mul_rn(delta, __ldg(K + k));
-                const T muv = __ldcg(mu + (size_t)a * im.mu_pitch + b);
-                const Dat4<T> dv = dt[(size_t)a * W + b];
-                accL += dl_pixel<T>(muv, xk, dv.c, dv.is2, dv.beta, bad);
-            }
-            dx += sdx;
-            dy += sdy;
-            if (dx >= L) { dx -= L; ++dy; }
-        }
-    }
-    accL = warp_sum(accL);
-
-    // a4: prior change for the patch holding (i, j)
-    T2* spec = reinterpret_cast<T2*>(ch.spec) + im.patch_off[p];
-    const int* ekl = im.ent_kl + sh.ent_off;
-    const T* ewa = ent_wa<T>(im) + sh.ent_off;
-    const T* em = ent_m<T>(im) + sh.ent_off;
-    const T2* twh = reinterpret_cast<const T2*>(twid<T>(im)) + sh.twh_off;
-    const T2* tww = reinterpret_cast<const T2*>(twid<T>(im)) + sh.tww_off;
-    T accP = (T)0, accS = (T)0, accA = (T)0;
-    for (int e = lane; e < sh.nhalf; e += 32) {
-        const int kl = __ldg(ekl + e);
-        const int k = kl >> 16, l = kl & 0xffff;
-        const T2 eh = twh[(k * u) % sh.ph], ew = tww[(l * v) % sh.pw];
-        const T wr = eh.x * ew.x - eh.y * ew.y, wi = eh.x * ew.y + eh.y * ew.x;
-        const T2 X = spec[e];
-        const T n2 = X.x * X.x + X.y * X.y;
-        const T dd = delta * ((T)2 * (X.x * wr + X.y * wi) + delta);   // |X'|^2 - |X|^2
-        const T rn = fma(delta, wr, X.x), in = fma(delta, wi, X.y);
-        const T n2n = rn * rn + in * in;
-        if (!(n2n > (T)0)) bad = true;
-        const T mo = P::sqrt(n2), mn = P::sqrt(n2n);
-        const T mult = __ldg(em + e);
-        accP += __ldg(ewa + e) * P::log1p(dd / n2);
-        accS += mult * (dd / (mn + mo));                               // |X'| - |X|
-        accA += mult * mo;
-    }
-    accP = warp_sum(accP);
-    accS = warp_sum(accS);
-    accA = warp_sum(accA);
-    const T dP = accP + (T)(sh.K - 1) * P::log1p(accS / accA);
-    bad = __any_sync(0xffffffffu, bad);
-
-    // a5: Metropolis-Hastings test with the Hastings term of the log-space walk
-    const bool accept = !bad && (lu < accL + dP + step * z);
-    if (accept) {
-        int dy = lane / L, dx = lane - (lane / L) * L;
-        for (int k = lane; k < LL; k += 32) {
-            const int a = a0 + dy, b = b0 + dx;
-            if ((unsigned)a < (unsigned)H && (unsigned)b < (unsigned)W) {
-                T* q = mu + (size_t)a * im.mu_pitch + b;
-                __stcg(q, add_rn(__ldcg(q), mul_rn(delta, __ldg(K + k))));
-            }
-            dx += sdx;
-            dy += sdy;
-            if (dx >= L) { dx -= L; ++dy; }
-        }
-        for (int e = lane; e < sh.nhalf; e += 32) {
-            const int kl = __ldg(ekl + e);
-            const int k = kl >> 16, l = kl & 0xffff;
-            const T2 eh = twh[(k * u) % sh.ph], ew = tww[(l * v) % sh.pw];
-            const T wr = eh.x * ew.x - eh.y * ew.y, wi = eh.x * ew.y + eh.y * ew.x;
-            T2 X = spec[e];
-            X.x = fma(delta, wr, X.x);
-            X.y = fma(delta, wi, X.y);
-            spec[e] = X;
-        }
-        if (lane == 0) {
-            rho[m] = r_new;
-            ch.trace_part[(size_t)slot * im.n_patches + p] += (double)accL + (double)dP;
-        }
-        ++n_acc;
-    }
-    if (ch.acc_log != nullptr && lane == 0)
-        ch.acc_log[(size_t)(t - 1) * im.Ho * im.Wo + m] = accept ? 1 : 0;
+    const T n2 = xr * xr + xi * xi;
+    const T dd = delta * ((T)2 * (xr * wr + xi * wi) + delta);
+    const T rn = fma(delta, wr, xr), in = fma(delta, wi, xi);
+    const T n2n = rn * rn + in * in;
+    if (!(n2n > (T)0)) bad = true;
+    const T mo = P::sqrt(n2), mn = P::sqrt(n2n);
+    accP += wa * P::log1p(dd / n2);
+    accS += mult * (dd / (mn + mo));
+    accA += mult * mo;
 }
 
 template <typename T>
+__device__ __forceinline__ void twiddle(const T* tw, const Shape& sh, int kl, int u, int v, T& wr, T& wi)
+{
+    const int k = kl >> 16, l = kl & 0xffff;
+    const T* eh = tw + 2 * (sh.twh_off + (k * u) % sh.ph);
+    const T* ew = tw + 2 * (sh.tww_off + (l * v) % sh.pw);
+    wr = eh[0] * ew[0] - eh[1] * ew[1];
+    wi = eh[0] * ew[1] + eh[1] * ew[0];
+}
+
+constexpr int kMaxPx = 4;   // window pixels per thread fetched in one batch
+
+template <typename T, bool RES>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
 {
+    using P = Prec<T>;
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_nbr[8];
     __shared__ int s_nn;
     __shared__ int s_abort;
     __shared__ int s_ci;
 
-    // locate this block's chain and tile
-    if (threadIdx.x == 0) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
         int lo = 0, hi = a.n_chains - 1;
         while (lo < hi) {   // last chain with cta_base <= blockIdx.x
             const int mid = (lo + hi + 1) >> 1;
@@ -162,24 +84,76 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
     const Image& im = a.imgs[ch.img];
     const int tl = (int)blockIdx.x - ch.cta_base;
     const int ti = tl / ch.ntj, tj = tl - (tl / ch.ntj) * ch.ntj;
-    if (threadIdx.x == 0) {
+    const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W, S2 = S * S, LL = L * L;
+    const int pi0 = ti * ch.tpi, pj0 = tj * ch.tpj;
+    const int pi1 = min(pi0 + ch.tpi, im.npi), pj1 = min(pj0 + ch.tpj, im.npj);
+    const int tw_ = pj1 - pj0, npt = (pi1 - pi0) * tw_;
+    // camera region seen by the tile's windows
+    const int i0 = pi0 * S, j0 = pj0 * S, i1 = min(pi1 * S, im.Ho), j1 = min(pj1 * S, im.Wo);
+    const int a_lo = max(0, i0 - 2 * R), a_hi = min(H, i1), b_lo = max(0, j0 - 2 * R), b_hi = min(W, j1);
+    const int rw = b_hi - b_lo;
+
+    const SmemPlan sp = smem_plan(L, S, im.n_tw, im.n_ent, im.max_nhalf, ch.tpi, ch.tpj, RES ? 1 : 0, sizeof(T));
+    T* red = reinterpret_cast<T*>(smem + sp.red);          // [2][8 sub-teams][8 warps][4]
+    T* Ks = reinterpret_cast<T*>(smem + sp.K);
+    T* tws = reinterpret_cast<T*>(smem + sp.tw);
+    int* ekl = reinterpret_cast<int*>(smem + sp.ekl);
+    T* ewa = reinterpret_cast<T*>(smem + sp.ewa);
+    T* em = reinterpret_cast<T*>(smem + sp.em);
+    T* spec_s = reinterpret_cast<T*>(smem + sp.spec);       // [npt][max_nhalf] complex
+    T* rho_s = reinterpret_cast<T*>(smem + sp.rho);         // [npt][S*S]
+    Dat4<T>* dat_s = reinterpret_cast<Dat4<T>*>(smem + sp.dat);
+
+    T* rho_g = reinterpret_cast<T*>(ch.rho);
+    T* mu_g = reinterpret_cast<T*>(ch.mu);
+    T* spec_g = reinterpret_cast<T*>(ch.spec);
+    const Dat4<T>* dat_g = dat<T>(im);
+
+    // ---- prologue: neighbours, tables, resident tile state
+    if (tid == 0) {
         int nn = 0;
         for (int di = -1; di <= 1; ++di)
             for (int dj = -1; dj <= 1; ++dj) {
                 const int ni = ti + di, nj = tj + dj;
-                if ((di || dj) && ni >= 0 && ni < ch.nti && nj >= 0 && nj < ch.ntj)
-                    s_nbr[nn++] = ni * ch.ntj + nj;
+                if ((di || dj) && ni >= 0 && ni < ch.nti && nj >= 0 && nj < ch.ntj) s_nbr[nn++] = ni * ch.ntj + nj;
             }
         s_nn = nn;
         s_abort = 0;
     }
+    for (int k = tid; k < LL; k += blockDim.x) Ks[k] = kern<T>(im)[k];
+    for (int k = tid; k < 2 * im.n_tw; k += blockDim.x) tws[k] = twid<T>(im)[k];
+    for (int k = tid; k < im.n_ent; k += blockDim.x) {
+        ekl[k] = im.ent_kl[k];
+        ewa[k] = ent_wa<T>(im)[k];
+        em[k] = ent_m<T>(im)[k];
+    }
+    if (RES) {
+        for (int k = tid; k < (a_hi - a_lo) * rw; k += blockDim.x) {
+            const int aa = k / rw, bb = k - (k / rw) * rw;
+            dat_s[k] = dat_g[(size_t)(a_lo + aa) * W + b_lo + bb];
+        }
+        for (int q = 0; q < npt; ++q) {
+            const int pi = pi0 + q / tw_, pj = pj0 + (q - (q / tw_) * tw_);
+            const Shape& sh = im.shape[shape_index(im, pi, pj)];
+            const T* src = spec_g + 2 * im.patch_off[pi * im.npj + pj];
+            for (int e = tid; e < 2 * sh.nhalf; e += blockDim.x) spec_s[(size_t)q * 2 * im.max_nhalf + e] = src[e];
+            for (int e = tid; e < sh.ph * sh.pw; e += blockDim.x) {
+                const int uu = e / sh.pw, vv = e - (e / sh.pw) * sh.pw;
+                rho_s[(size_t)q * S2 + uu * S + vv] = rho_g[(size_t)(pi * S + uu) * im.Wo + pj * S + vv];
+            }
+        }
+    }
     __syncthreads();
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int pi0 = ti * ch.tpi, pj0 = tj * ch.tpj;
-    const int pi1 = min(pi0 + ch.tpi, im.npi), pj1 = min(pj0 + ch.tpj, im.npj);
-    const int tw_ = pj1 - pj0, npt = (pi1 - pi0) * tw_;
-    const int S = im.S, S2 = S * S;
+    const int NT = team_threads(L);
+    const int n_sub = max(1, (int)blockDim.x / NT);
+    const int g = tid / NT, lt = tid - (tid / NT) * NT;
+    const bool in_team = g < n_sub;
+    const int twarp = lt >> 5, lane = tid & 31, nwt = NT >> 5;
+    const int rounds = (npt + n_sub - 1) / n_sub;
+    T* red1 = red + (size_t)(g * 8) * 4;                   // prior partials of this sub-team
+    T* red2 = red + 8 * 8 * 4 + (size_t)(g * 8) * 4;       // likelihood partials
+    const T step = (T)im.step;
     const int nsteps = a.n_sweeps * S2;
     int n_acc = 0;
 
@@ -187,139 +161,279 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
         const int slot = s / S2, c = s - slot * S2;
         const int t = a.t0 + 1 + slot;
         const int u = c / S, v = c - (c / S) * S;
-        if (s > 0) {
-            if (warp == 0) {
+        for (int r = 0; r < rounds; ++r) {
+            const int q = r * n_sub + g;
+            bool active = in_team && q < npt;
+            int pi = 0, pj = 0, sidx = 0;
+            if (active) {
+                pi = pi0 + q / tw_;
+                pj = pj0 + (q - (q / tw_) * tw_);
+                sidx = shape_index(im, pi, pj);
+                active = u < im.shape[sidx].ph && v < im.shape[sidx].pw;
+            }
+            const Shape& sh = im.shape[sidx];
+            const int i = pi * S + u, j = pj * S + v;
+            const int m = i * im.Wo + j;
+            T z = 0, lu = 0, r_old = 0, r_new = 0, delta = 0;
+            bool badP = false;
+            T* spec_p = RES ? spec_s + (size_t)q * 2 * im.max_nhalf : spec_g + 2 * im.patch_off[pi * im.npj + pj];
+            // a2 + a4: proposal and prior change (own tile state only)
+            if (active) {
+                const uint4 x = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)t, (uint32_t)ch.chain, 0u),
+                                              im.seed_lo, im.seed_hi);
+                z = P::gauss(uniform23<T>(x.x), uniform23<T>(x.y));
+                lu = P::log(uniform23<T>(x.z));
+                r_old = RES ? rho_s[(size_t)q * S2 + u * S + v] : rho_g[m];
+                r_new = r_old * P::exp(step * z);
+                delta = r_new - r_old;
+                T accP = 0, accS = 0, accA = 0;
+                for (int e = lt; e < sh.nhalf; e += NT) {
+                    T wr, wi;
+                    const int ent = sh.ent_off + e;
+                    twiddle(tws, sh, ekl[ent], u, v, wr, wi);
+                    prior_term<T>(spec_p[2 * e], spec_p[2 * e + 1], wr, wi, delta, ewa[ent], em[ent], accP, accS,
+                                  accA, badP);
+                }
+                accP = warp_sum(accP);
+                accS = warp_sum(accS);
+                accA = warp_sum(accA);
+                const bool wb = __any_sync(0xffffffffu, badP);
+                if (lane == 0) {
+                    red1[twarp * 4 + 0] = accP;
+                    red1[twarp * 4 + 1] = accS;
+                    red1[twarp * 4 + 2] = accA;
+                    red1[twarp * 4 + 3] = wb ? (T)1 : (T)0;
+                }
+            }
+            if (r == 0 && s > 0 && tid < 32) {
                 const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err);
                 if (lane == 0 && !ok) s_abort = 1;
             }
             __syncthreads();
             if (s_abort) return;
-        }
-        for (int q = warp; q < npt; q += nw) {
-            const int pi = pi0 + q / tw_, pj = pj0 + (q - (q / tw_) * tw_);
-            update_pixel<T>(im, ch, pi, pj, u, v, t, slot, n_acc);
+            // a3: likelihood change over the PSF window
+            T muv[kMaxPx];
+            T dP = 0;
+            bool bad = false;
+            if (active) {
+                T sP = 0, sS = 0, sA = 0;
+                for (int w = 0; w < nwt; ++w) {
+                    sP += red1[w * 4 + 0];
+                    sS += red1[w * 4 + 1];
+                    sA += red1[w * 4 + 2];
+                    bad = bad || red1[w * 4 + 3] != (T)0;
+                }
+                dP = sP + (T)(sh.K - 1) * P::log1p(sS / sA);
+                T accL = 0;
+                bool badL = false;
+                for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
+#pragma unroll
+                    for (int jj = 0; jj < kMaxPx; ++jj) {
+                        const int k = k0 + jj * NT;
+                        const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
+                        muv[jj] = (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W)
+                                      ? __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb) : (T)-1;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < kMaxPx; ++jj) {
+                        const int k = k0 + jj * NT;
+                        const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
+                        if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
+                            const Dat4<T> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
+                            accL += dl_pixel<T>(muv[jj], mul_rn(delta, Ks[k]), dv.c, dv.is2, dv.beta, badL);
+                        }
+                    }
+                }
+                accL = warp_sum(accL);
+                const bool wb = __any_sync(0xffffffffu, badL);
+                if (lane == 0) {
+                    red2[twarp * 4 + 0] = accL;
+                    red2[twarp * 4 + 1] = wb ? (T)1 : (T)0;
+                }
+            }
+            __syncthreads();
+            // a5: Metropolis-Hastings decision with the Hastings term of the log-space walk
+            if (active) {
+                T dL = 0;
+                for (int w = 0; w < nwt; ++w) {
+                    dL += red2[w * 4 + 0];
+                    bad = bad || red2[w * 4 + 1] != (T)0;
+                }
+                const bool accept = !bad && (lu < dL + dP + step * z);
+                if (accept) {
+                    const bool one_batch = LL <= NT * kMaxPx;
+                    for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
+#pragma unroll
+                        for (int jj = 0; jj < kMaxPx; ++jj) {
+                            const int k = k0 + jj * NT;
+                            const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
+                            if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
+                                // same value the proposal was scored with: still in registers when
+                                // the window took one batch, else reloaded (unchanged since)
+                                const T old = one_batch ? muv[jj] : __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb);
+                                __stcg(mu_g + (size_t)aa * im.mu_pitch + bb, add_rn(old, mul_rn(delta, Ks[k])));
+                            }
+                        }
+                    }
+                    for (int e = lt; e < sh.nhalf; e += NT) {
+                        T wr, wi;
+                        twiddle(tws, sh, ekl[sh.ent_off + e], u, v, wr, wi);
+                        spec_p[2 * e] = fma(delta, wr, spec_p[2 * e]);
+                        spec_p[2 * e + 1] = fma(delta, wi, spec_p[2 * e + 1]);
+                    }
+                    if (lt == 0) {
+                        if (RES) rho_s[(size_t)q * S2 + u * S + v] = r_new;
+                        rho_g[m] = r_new;
+                        ch.trace_part[(size_t)slot * im.n_patches + pi * im.npj + pj] += (double)dL + (double)dP;
+                        ++n_acc;
+                    }
+                }
+                if (ch.acc_log != nullptr && lt == 0) ch.acc_log[(size_t)(t - 1) * im.Ho * im.Wo + m] = accept ? 1 : 0;
+            }
+            __syncthreads();
         }
         if (c == S2 - 1) {
-            __syncwarp();
             // a7: after the sweep, add the object to the running sums (own patches only)
             if (t > im.burn_in) {
-                const T* rho = reinterpret_cast<const T*>(ch.rho);
-                for (int q = warp; q < npt; q += nw) {
+                for (int q = 0; q < npt; ++q) {
                     const int pi = pi0 + q / tw_, pj = pj0 + (q - (q / tw_) * tw_);
                     const Shape& sh = im.shape[shape_index(im, pi, pj)];
-                    for (int e = lane; e < sh.ph * sh.pw; e += 32) {
+                    for (int e = tid; e < sh.ph * sh.pw; e += blockDim.x) {
                         const int uu = e / sh.pw, vv = e - (e / sh.pw) * sh.pw;
                         const size_t mm = (size_t)(pi * S + uu) * im.Wo + pj * S + vv;
-                        const double rv = (double)rho[mm];
+                        const double rv = RES ? (double)rho_s[(size_t)q * S2 + uu * S + vv] : (double)rho_g[mm];
                         ch.rho_sum[mm] += rv;
                         if (ch.rho_sq) ch.rho_sq[mm] += rv * rv;
                     }
                 }
             }
-            if (lane == 0 && n_acc) atomicAdd(ch.acc_count + (t - 1), (unsigned long long)n_acc);
+            if (lt == 0 && in_team && n_acc) atomicAdd(ch.acc_count + (t - 1), (unsigned long long)n_acc);
             n_acc = 0;
+            __syncthreads();
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        if (tid == 0) {
             __threadfence();
             st_release(ch.prog + tl, s + 1);
+        }
+    }
+    // ---- epilogue: resident spectra back to global memory
+    if (RES) {
+        for (int q = 0; q < npt; ++q) {
+            const int pi = pi0 + q / tw_, pj = pj0 + (q - (q / tw_) * tw_);
+            const Shape& sh = im.shape[shape_index(im, pi, pj)];
+            T* dst = spec_g + 2 * im.patch_off[pi * im.npj + pj];
+            for (int e = tid; e < 2 * sh.nhalf; e += blockDim.x) dst[e] = spec_s[(size_t)q * 2 * im.max_nhalf + e];
         }
     }
 }
 
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs& a, int grid, int warps, cudaStream_t st)
+cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st)
 {
     SweepArgs args = a;
     void* kargs[] = {&args};
-    return cudaLaunchCooperativeKernel((const void*)k_sweep<T>, dim3(grid), dim3(32 * warps), kargs,
-                                       0, st);
+    const void* fn = a.resident ? (const void*)k_sweep<T, true> : (const void*)k_sweep<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), kargs, smem, st);
 }
 
 template <typename T>
-int sweep_blocks_per_sm(int warps)
+int sweep_blocks_per_sm(int threads, size_t smem)
 {
-    int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T>, 32 * warps, 0) != cudaSuccess)
-        return 0;
-    return n;
+    int n = 0, n2 = 0;
+    const void* fn = (const void*)k_sweep<T, true>;
+    const void* fn2 = (const void*)k_sweep<T, false>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(fn2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, true>, threads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_sweep<T, false>, threads, smem) != cudaSuccess) return 0;
+    return n < n2 ? n : n2;
 }
 
-template cudaError_t launch_sweep<float>(const SweepArgs&, int, int, cudaStream_t);
-template cudaError_t launch_sweep<double>(const SweepArgs&, int, int, cudaStream_t);
-template int sweep_blocks_per_sm<float>(int);
-template int sweep_blocks_per_sm<double>(int);
+template cudaError_t launch_sweep<float>(const SweepArgs&, int, int, size_t, cudaStream_t);
+template cudaError_t launch_sweep<double>(const SweepArgs&, int, int, size_t, cudaStream_t);
+template int sweep_blocks_per_sm<float>(int, size_t);
+template int sweep_blocks_per_sm<double>(int, size_t);
 
 // ---------------------------------------------------------------- delta --
-// The same per-update arithmetic for one hypothetical proposal (testing).
+// The same per-update arithmetic for one hypothetical proposal (testing):
+// one team, the same pixel and entry assignment and reduction order.
 template <typename T>
-__global__ void k_delta(const Image* imp, const Chain* chp, int64_t m, double rho_new, double* out)
+__global__ void __launch_bounds__(256) k_delta(const Image* imp, const Chain* chp, int64_t m, double rho_new, double* out)
 {
     using P = Prec<T>;
-    using T2 = typename Vec2<T>::type;
+    __shared__ T red[8][4];
+    __shared__ int s_bad;
     const Image& im = *imp;
     const Chain& ch = *chp;
-    const int lane = threadIdx.x & 31;
+    const int lt = threadIdx.x, lane = lt & 31, twarp = lt >> 5;
+    const int NT = team_threads(im.L), nwt = NT >> 5;
     const int i = (int)(m / im.Wo), j = (int)(m % im.Wo);
-    const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W;
+    const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L;
     const int pi = i / S, pj = j / S, u = i - pi * S, v = j - pj * S;
-    const int p = pi * im.npj + pj;
     const Shape& sh = im.shape[shape_index(im, pi, pj)];
     const T* rho = reinterpret_cast<const T*>(ch.rho);
     const T delta = (T)rho_new - rho[m];
     const T* K = kern<T>(im);
     const Dat4<T>* dt = dat<T>(im);
     const T* mu = reinterpret_cast<const T*>(ch.mu);
-    bool bad = false;
-    T accL = (T)0;
-    for (int k = lane; k < L * L; k += 32) {
-        const int a = i - 2 * R + k / L, b = j - 2 * R + k % L;
-        if ((unsigned)a < (unsigned)H && (unsigned)b < (unsigned)W) {
-            const Dat4<T> dv = dt[(size_t)a * W + b];
-            accL += dl_pixel<T>(mu[(size_t)a * im.mu_pitch + b], mul_rn(delta, K[k]), dv.c, dv.is2, dv.beta, bad);
+    const T* spec = reinterpret_cast<const T*>(ch.spec) + 2 * im.patch_off[pi * im.npj + pj];
+    if (lt == 0) s_bad = 0;
+    bool badP = false, badL = false;
+    T accP = 0, accS = 0, accA = 0, accL = 0;
+    for (int e = lt; e < sh.nhalf; e += NT) {
+        T wr, wi;
+        const int ent = sh.ent_off + e;
+        twiddle(twid<T>(im), sh, im.ent_kl[ent], u, v, wr, wi);
+        prior_term<T>(spec[2 * e], spec[2 * e + 1], wr, wi, delta, ent_wa<T>(im)[ent], ent_m<T>(im)[ent], accP, accS,
+                      accA, badP);
+    }
+    for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx)
+        for (int jj = 0; jj < kMaxPx; ++jj) {
+            const int k = k0 + jj * NT;
+            const int aa = i - 2 * R + k / L, bb = j - 2 * R + k % L;
+            if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
+                const Dat4<T> dv = dt[(size_t)aa * W + bb];
+                accL += dl_pixel<T>(mu[(size_t)aa * im.mu_pitch + bb], mul_rn(delta, K[k]), dv.c, dv.is2, dv.beta, badL);
+            }
         }
-    }
-    accL = warp_sum(accL);
-    const T2* spec = reinterpret_cast<const T2*>(ch.spec) + im.patch_off[p];
-    const T2* twh = reinterpret_cast<const T2*>(twid<T>(im)) + sh.twh_off;
-    const T2* tww = reinterpret_cast<const T2*>(twid<T>(im)) + sh.tww_off;
-    T accP = (T)0, accS = (T)0, accA = (T)0;
-    for (int e = lane; e < sh.nhalf; e += 32) {
-        const int kl = im.ent_kl[sh.ent_off + e];
-        const int k = kl >> 16, l = kl & 0xffff;
-        const T2 eh = twh[(k * u) % sh.ph], ew = tww[(l * v) % sh.pw];
-        const T wr = eh.x * ew.x - eh.y * ew.y, wi = eh.x * ew.y + eh.y * ew.x;
-        const T2 X = spec[e];
-        const T n2 = X.x * X.x + X.y * X.y;
-        const T dd = delta * ((T)2 * (X.x * wr + X.y * wi) + delta);
-        const T rn = fma(delta, wr, X.x), in = fma(delta, wi, X.y);
-        const T n2n = rn * rn + in * in;
-        if (!(n2n > (T)0)) bad = true;
-        const T mo = P::sqrt(n2), mn = P::sqrt(n2n);
-        const T mult = ent_m<T>(im)[sh.ent_off + e];
-        accP += ent_wa<T>(im)[sh.ent_off + e] * P::log1p(dd / n2);
-        accS += mult * (dd / (mn + mo));
-        accA += mult * mo;
-    }
     accP = warp_sum(accP);
     accS = warp_sum(accS);
     accA = warp_sum(accA);
-    bad = __any_sync(0xffffffffu, bad);
+    accL = warp_sum(accL);
+    const bool b = __any_sync(0xffffffffu, badP || badL);
+    __syncthreads();
     if (lane == 0) {
-        out[0] = (double)accL;
-        out[1] = (double)(accP + (T)(sh.K - 1) * P::log1p(accS / accA));
-        out[2] = bad ? 0.0 : 1.0;
+        red[twarp][0] = accP;
+        red[twarp][1] = accS;
+        red[twarp][2] = accA;
+        red[twarp][3] = accL;
+        if (b) atomicOr(&s_bad, 1);
+    }
+    __syncthreads();
+    if (lt == 0) {
+        T sP = 0, sS = 0, sA = 0, sL = 0;
+        for (int w = 0; w < nwt; ++w) {
+            sP += red[w][0];
+            sS += red[w][1];
+            sA += red[w][2];
+            sL += red[w][3];
+        }
+        out[0] = (double)sL;
+        out[1] = (double)(sP + (T)(sh.K - 1) * P::log1p(sS / sA));
+        out[2] = s_bad ? 0.0 : 1.0;
     }
 }
 
 template <typename T>
-void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3,
+void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3, int L,
                   cudaStream_t st, int64_t* launches)
 {
-    k_delta<T><<<1, 32, 0, st>>>(d_im, d_ch, m, rho_new, out3);
+    k_delta<T><<<1, team_threads(L), 0, st>>>(d_im, d_ch, m, rho_new, out3);
     ++*launches;
 }
-template void launch_delta<float>(const Image*, const Chain*, int64_t, double, double*, cudaStream_t, int64_t*);
-template void launch_delta<double>(const Image*, const Chain*, int64_t, double, double*, cudaStream_t, int64_t*);
+template void launch_delta<float>(const Image*, const Chain*, int64_t, double, double*, int, cudaStream_t, int64_t*);
+template void launch_delta<double>(const Image*, const Chain*, int64_t, double, double*, int, cudaStream_t, int64_t*);
 
 }  // namespace bd

@@ -29,6 +29,7 @@ struct ProbHost {
     std::vector<int64_t> patch_off;
     int64_t spec_len = 0;
     int n_tw = 0;               // complex twiddle entries
+    int max_nhalf = 0;
     // arena offsets (bytes)
     size_t o_K64, o_K32, o_dat64, o_dat32, o_ekl, o_wa64, o_m64, o_wa32, o_m32, o_tw64, o_tw32, o_poff;
     size_t o_sum, o_sq, o_scr;
@@ -53,6 +54,9 @@ struct bdecon_handle {
     int warps = 1;
     bool user_warps = false;
     int grid = 0;
+    int threads = 32;
+    size_t smem = 0;
+    int resident = 1;
     bool failed = false;
     int sms = 0;
     cudaStream_t st = nullptr;
@@ -171,6 +175,7 @@ void describe(ProbHost& ph)
     const int rh = ph.Ho - (ph.npi - 1) * ph.S, rw = ph.Wo - (ph.npj - 1) * ph.S;   // last patch sides
     int twoff = 0;
     ph.ent_kl.clear();
+    ph.max_nhalf = 0;
     for (int s = 0; s < kMaxShapes; ++s) {
         Shape& sh = ph.shape[s];
         const bool pr = (s & 2) != 0, pc = (s & 1) != 0;
@@ -184,6 +189,7 @@ void describe(ProbHost& ph)
         sh.ent_off = (int)ph.ent_kl.size();
         half_entries(sh.ph, sh.pw, ph.ent_kl);
         sh.nhalf = (int)ph.ent_kl.size() - sh.ent_off;
+        ph.max_nhalf = std::max(ph.max_nhalf, sh.nhalf);
         sh.twh_off = twoff; twoff += sh.ph;
         sh.tww_off = twoff; twoff += sh.pw;
     }
@@ -204,35 +210,77 @@ int blocks_of(const ProbHost& ph)
     return ph.p.n_chains * ((ph.npi + ph.tpi - 1) / ph.tpi) * ((ph.npj + ph.tpj - 1) / ph.tpj);
 }
 
-int occupancy(int prec, int warps)
+int occupancy(int prec, int threads, size_t smem)
 {
-    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(warps) : sweep_blocks_per_sm<double>(warps);
+    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem) : sweep_blocks_per_sm<double>(threads, smem);
 }
 
-// automatic plan: one patch per tile and one warp per block while everything
-// fits co-resident; otherwise grow the tiles of the problem with the most
-// blocks until the whole batch fits.
+constexpr size_t kMaxSmem = 227 * 1024;
+
+size_t plan_smem(const bdecon_handle* h, int resident)
+{
+    const int ts = h->precision == BDECON_FP32 ? 4 : 8;
+    size_t mx = 0;
+    for (const auto& ph : h->probs) {
+        const SmemPlan sp = smem_plan(ph.L, ph.S, ph.n_tw, (int)ph.ent_kl.size(), ph.max_nhalf, ph.tpi, ph.tpj,
+                                      resident, ts);
+        mx = std::max(mx, sp.total);
+    }
+    return mx;
+}
+
+// Grow the tile of the problem with the most blocks; false if none can grow.
+bool grow_worst(bdecon_handle* h)
+{
+    int worst = -1, wb = -1;
+    for (size_t k = 0; k < h->probs.size(); ++k) {
+        const ProbHost& ph = h->probs[k];
+        const int b = blocks_of(ph);
+        if (!ph.user_plan && !(ph.tpi >= ph.npi && ph.tpj >= ph.npj) && b > wb) { wb = b; worst = (int)k; }
+    }
+    if (worst < 0) return false;
+    ProbHost& ph = h->probs[worst];
+    if ((ph.tpj <= ph.tpi && ph.tpj < ph.npj) || ph.tpi >= ph.npi) ++ph.tpj; else ++ph.tpi;
+    return true;
+}
+
+// Launch plan: block = the largest update team of the batch (or the user's
+// warps); tiles grow from one patch until every block of every chain is
+// co-resident.  Resident plans (tile state in shared memory) are preferred;
+// if none fits, tile state is streamed from global memory.
 bdecon_status make_plan(bdecon_handle* h)
 {
-    if (!h->user_warps) h->warps = 1;
-    const int bps = occupancy(h->precision, h->warps);
-    if (bps <= 0) return fail(h, BDECON_ERR_CUDA, "occupancy query failed for %d warps", h->warps);
-    const int cap = bps * h->sms;
-    for (auto& ph : h->probs)
-        if (!ph.user_plan) ph.tpi = ph.tpj = 1;
-    for (;;) {
-        int tot = 0, worst = -1, wb = -1;
-        for (size_t k = 0; k < h->probs.size(); ++k) {
-            const int b = blocks_of(h->probs[k]);
-            tot += b;
-            if (!h->probs[k].user_plan && b > wb) { wb = b; worst = (int)k; }
+    int team = 32;
+    for (const auto& ph : h->probs) team = std::max(team, team_threads(ph.L));
+    h->threads = h->user_warps ? std::max(32 * h->warps, team) : team;
+    h->warps = h->threads / 32;
+    bool done = false;
+    for (int resident = 1; resident >= 0 && !done; --resident) {
+        for (auto& ph : h->probs)
+            if (!ph.user_plan) ph.tpi = ph.tpj = 1;
+        for (;;) {
+            const size_t smem = plan_smem(h, resident);
+            int tot = 0;
+            for (const auto& ph : h->probs) tot += blocks_of(ph);
+            if (smem <= kMaxSmem) {
+                const int bps = occupancy(h->precision, h->threads, smem);
+                if (bps > 0 && tot <= bps * h->sms) {
+                    h->smem = smem;
+                    h->resident = resident;
+                    done = true;
+                    break;
+                }
+            } else if (resident) {
+                break;   // tiles only grow: resident state will not fit
+            }
+            if (!grow_worst(h)) break;
         }
-        if (tot <= cap) { h->grid = tot; break; }
-        if (worst < 0) return fail(h, BDECON_ERR_INVALID, "plan needs %d co-resident blocks, at most %d fit", tot, cap);
-        ProbHost& ph = h->probs[worst];
-        if (ph.tpi >= ph.npi && ph.tpj >= ph.npj)
-            return fail(h, BDECON_ERR_INVALID, "batch too large for one co-resident launch (%d blocks, %d fit)", tot, cap);
-        if ((ph.tpj <= ph.tpi && ph.tpj < ph.npj) || ph.tpi >= ph.npi) ++ph.tpj; else ++ph.tpi;
+    }
+    if (!done) {
+        int tot = 0;
+        for (const auto& ph : h->probs) tot += blocks_of(ph);
+        return fail(h, BDECON_ERR_INVALID, "no launch plan: %d blocks of %d threads cannot all be co-resident", tot,
+                    h->threads);
     }
     int base = 0;
     for (size_t k = 0; k < h->probs.size(); ++k) {
@@ -405,6 +453,9 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         im.tw64 = (const double*)(A + ph.o_tw64); im.tw32 = (const float*)(A + ph.o_tw32);
         im.patch_off = (const int64_t*)(A + ph.o_poff);
         im.spec_len = ph.spec_len;
+        im.n_ent = (int)ph.ent_kl.size();
+        im.n_tw = ph.n_tw;
+        im.max_nhalf = ph.max_nhalf;
     }
     h->chains.resize(h->chh.size());
     for (int k = 0; k < n; ++k) {
@@ -561,7 +612,7 @@ bdecon_status bdecon_sweep(bdecon_handle* h, int32_t n)
         }
         SweepArgs a;
         a.imgs = h->d_imgs; a.chains = h->d_chains; a.n_chains = (int)h->chains.size();
-        a.t0 = t0; a.n_sweeps = len; a.err = h->d_err;
+        a.t0 = t0; a.n_sweeps = len; a.err = h->d_err; a.resident = h->resident;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (h->timing) {
             if (h->ev_used + 2 > h->ev_pool.size()) {
@@ -576,10 +627,12 @@ bdecon_status bdecon_sweep(bdecon_handle* h, int32_t n)
             h->ev_used += 2;
             CK(h, cudaEventRecord(ev0, h->st));
         }
-        cudaError_t e = h->precision == BDECON_FP32 ? launch_sweep<float>(a, h->grid, h->warps, h->st)
-                                                    : launch_sweep<double>(a, h->grid, h->warps, h->st);
+        cudaError_t e = h->precision == BDECON_FP32 ? launch_sweep<float>(a, h->grid, h->threads, h->smem, h->st)
+                                                    : launch_sweep<double>(a, h->grid, h->threads, h->smem, h->st);
         if (h->timing) CK(h, cudaEventRecord(ev1, h->st));
-        if (e != cudaSuccess) return fail(h, BDECON_ERR_CUDA, "sweep launch (%d blocks x %d warps): %s", h->grid, h->warps, cudaGetErrorString(e));
+        if (e != cudaSuccess)
+            return fail(h, BDECON_ERR_CUDA, "sweep launch (%d blocks x %d threads, %zu B shared): %s", h->grid,
+                        h->threads, h->smem, cudaGetErrorString(e));
         ++h->launches;
         launch_trace(h->d_imgs, h->d_chains, (int)h->chains.size(), t0, len, h->st, &h->launches);
         CK(h, cudaGetLastError());
@@ -763,8 +816,8 @@ bdecon_status bdecon_delta(bdecon_handle* h, int32_t p, int32_t c, int64_t m, do
     const ProbHost& ph = h->probs[p];
     if (m < 0 || m >= (int64_t)ph.Ho * ph.Wo) return fail(h, BDECON_ERR_INVALID, "pixel %lld out of range", (long long)m);
     if (!(std::isfinite(rho_new) && rho_new > 0.0)) return fail(h, BDECON_ERR_INVALID, "rho_new must be finite and > 0");
-    if (h->precision == BDECON_FP32) launch_delta<float>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, h->st, &h->launches);
-    else launch_delta<double>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, h->st, &h->launches);
+    if (h->precision == BDECON_FP32) launch_delta<float>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, ph.L, h->st, &h->launches);
+    else launch_delta<double>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, ph.L, h->st, &h->launches);
     CK(h, cudaGetLastError());
     double r[3];
     CK(h, cudaMemcpyAsync(r, h->d_out, sizeof r, cudaMemcpyDeviceToHost, h->st));
