@@ -224,6 +224,42 @@ bdecon_status bdecon_launch_count(const bdecon_handle* h, int64_t* launches);
 bdecon_status bdecon_set_timing(bdecon_handle* h, int32_t enable);
 bdecon_status bdecon_sweep_kernel_time(bdecon_handle* h, double* ms, int64_t* launches);
 
+/* ----------------------------------------------------- allocation-free */
+
+/* Log posterior of Eq. 9 (the same quantity as bdecon_log_posterior) for an
+ * object held in device memory, without allocating any device memory.  The
+ * paper has no counterpart to this entry point: it exists for callers that
+ * must not call cudaMalloc or cudaFree once running -- for example an
+ * acquisition loop that reserved all device memory for frame buffers up
+ * front, or a host whose device allocator belongs to another framework and
+ * forbids outside allocations and the device synchronisation they can
+ * cause.  Creating a handle allocates, so such callers cannot use
+ * bdecon_log_posterior.
+ *
+ * Arguments mirror bdecon_problem, but every array is a DEVICE pointer:
+ * image, gain_map, offset_map, var_map (H*W float, maps may be NULL to use
+ * the scalar), psf (L*L double, >= 0, sum > 0; normalised here), rho
+ * ((H+2R)*(W+2R) double, > 0) and out (one double, written on the stream).
+ * Input values are not checked on the host (that would need a copy);
+ * invalid values give a non-finite result.  Work is queued on stream
+ * (cudaStream_t or NULL); the call returns without waiting.
+ *
+ * Scratch comes from one fixed array of 2^19 doubles (4 MiB) in the
+ * library's device memory, held by every GPU that loads the library until
+ * the process exits.  A problem needing more (L*L + 5*S*S + ceil(H*W/256) +
+ * patches doubles; about 8 megapixel frames at most) is refused with
+ * BDECON_ERR_INVALID and a message from bdecon_last_error(NULL).  The first
+ * call on each device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it and must be serialised by the caller.               */
+bdecon_status bdecon_log_posterior_static(int32_t H, int32_t W, const float* image, int32_t L,
+                                          const double* psf, const float* gain_map, double gain,
+                                          const float* offset_map, double offset,
+                                          const float* var_map, double read_var, int32_t stride,
+                                          const double* rho, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

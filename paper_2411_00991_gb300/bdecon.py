@@ -47,7 +47,8 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_posterior_mean", "bdecon_posterior_var", "bdecon_log_posterior_trace",
            "bdecon_accept_counts", "bdecon_accept_log", "bdecon_get_state", "bdecon_set_state",
            "bdecon_get_mu", "bdecon_log_posterior", "bdecon_delta", "bdecon_set_plan",
-           "bdecon_get_plan", "bdecon_launch_count", "bdecon_set_timing", "bdecon_sweep_kernel_time"]
+           "bdecon_get_plan", "bdecon_launch_count", "bdecon_set_timing", "bdecon_sweep_kernel_time",
+           "bdecon_log_posterior_static"]
 
 
 def lib_path() -> str:
@@ -89,6 +90,8 @@ def load(build_if_missing: bool = True):
         "bdecon_launch_count": [H, C.POINTER(i64)],
         "bdecon_set_timing": [H, i32],
         "bdecon_sweep_kernel_time": [H, dp, C.POINTER(i64)],
+        "bdecon_log_posterior_static": [i32, i32, vp, i32, vp, vp, C.c_double, vp, C.c_double, vp,
+                                        C.c_double, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -113,6 +116,30 @@ def _as_map_or_scalar(v, H, W):
     if a.shape != (H, W):
         raise ValueError(f"map shape {a.shape} != {(H, W)}")
     return a, 0.0
+
+
+def log_posterior_static(H, W, image_ptr, L, psf_ptr, gain, offset, var, stride, rho_ptr, out_ptr,
+                         stream=None):
+    """Allocation-free log posterior (bdecon_log_posterior_static): every
+    array argument is a device pointer (int); gain / offset / var are a
+    device-pointer int for a map or a float scalar (pass ``("map", ptr)``
+    for a map).  Returns nothing: the value is written to out_ptr on the
+    stream."""
+    L_ = load()
+
+    def split(x):
+        if isinstance(x, tuple):
+            return C.c_void_p(x[1]), 0.0
+        return None, float(x)
+
+    g, gs = split(gain)
+    o, os_ = split(offset)
+    v, vs = split(var)
+    s = L_.bdecon_log_posterior_static(int(H), int(W), C.c_void_p(image_ptr), int(L), C.c_void_p(psf_ptr), g, gs,
+                                       o, os_, v, vs, int(stride), C.c_void_p(rho_ptr), C.c_void_p(out_ptr),
+                                       C.c_void_p(stream) if stream else None)
+    if s != 0:
+        raise BdeconError(s, L_.bdecon_last_error(None).decode())
 
 
 class Sampler:

@@ -146,6 +146,8 @@ void launch_convert(const void* src, double* dst, int64_t n, int rows, int cols,
                     cudaStream_t st, int64_t* launches);
 template <typename T>
 void launch_set_rho(const double* src, void* dst, int64_t n, cudaStream_t st, int64_t* launches);
+// sets the thread-local message that bdecon_last_error(NULL) returns
+void set_host_error(const char* msg);
 void launch_mean(const double* sum, int n_chains_img, int64_t chain_stride_elems, int Ho, int Wo,
                  int crop_r, int out_h, int out_w, double inv_n, double* out, const double* sq,
                  int want_var, cudaStream_t st, int64_t* launches);

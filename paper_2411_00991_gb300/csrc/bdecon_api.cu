@@ -18,6 +18,12 @@ namespace {
 
 thread_local std::string g_err;
 
+}  // namespace
+
+void bd::set_host_error(const char* msg) { g_err = msg; }
+
+namespace {
+
 struct ProbHost {
     bdecon_problem p;           // copy (host pointers not retained)
     int H, W, L, R, S, Ho, Wo, npi, npj, n_patches, pitch;
