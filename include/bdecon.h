@@ -217,6 +217,16 @@ bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int3
 /* Kernel launches issued by this handle since creation.                    */
 bdecon_status bdecon_launch_count(const bdecon_handle* h, int64_t* launches);
 
+/* Failure-detection test knob.  Every wait of a thread block for its
+ * neighbours is bounded (default 4 s): past the limit the block raises the
+ * device error flag and returns, the other blocks see the flag and return
+ * too, and the host reads BDECON_ERR_TIMEOUT at the next sync; the CUDA
+ * context stays usable.  silent_block >= 0 makes that block of the sweep
+ * kernel never publish its progress, so its neighbours' waits run out;
+ * wait_ns sets the wait limit (1 ms .. 60 s).  silent_block = -1 restores
+ * normal operation.                                                        */
+bdecon_status bdecon_set_fault(bdecon_handle* h, int32_t silent_block, int64_t wait_ns);
+
 /* Per-kernel timing: while enabled, CUDA events on the handle's stream
  * bracket every launch of the sweep kernel.  bdecon_sweep_kernel_time
  * synchronises, returns the summed device time (ms) and the number of

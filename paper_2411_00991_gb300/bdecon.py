@@ -48,7 +48,7 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_accept_counts", "bdecon_accept_log", "bdecon_get_state", "bdecon_set_state",
            "bdecon_get_mu", "bdecon_log_posterior", "bdecon_delta", "bdecon_set_plan",
            "bdecon_get_plan", "bdecon_launch_count", "bdecon_set_timing", "bdecon_sweep_kernel_time",
-           "bdecon_log_posterior_static"]
+           "bdecon_log_posterior_static", "bdecon_set_fault"]
 
 
 def lib_path() -> str:
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = True):
         "bdecon_launch_count": [H, C.POINTER(i64)],
         "bdecon_set_timing": [H, i32],
         "bdecon_sweep_kernel_time": [H, dp, C.POINTER(i64)],
+        "bdecon_set_fault": [H, i32, i64],
         "bdecon_log_posterior_static": [i32, i32, vp, i32, vp, vp, C.c_double, vp, C.c_double, vp,
                                         C.c_double, i32, vp, vp, vp],
     }
@@ -304,6 +305,9 @@ class Sampler:
         b, w, ti, tj = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         self._ck(self.L.bdecon_get_plan(self.h, p, C.byref(b), C.byref(w), C.byref(ti), C.byref(tj)))
         return dict(blocks=b.value, warps=w.value, tile_i=ti.value, tile_j=tj.value)
+
+    def set_fault(self, silent_block: int, wait_ns: int = 4_000_000_000):
+        self._ck(self.L.bdecon_set_fault(self.h, int(silent_block), int(wait_ns)))
 
     def set_timing(self, enable: bool = True):
         self._ck(self.L.bdecon_set_timing(self.h, int(bool(enable))))

@@ -134,6 +134,10 @@ __device__ __forceinline__ void st_release(int* p, int v)
 {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_relaxed(int* p, int v)
+{
+    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ int ld_relaxed(const int* p)
 {
     int v;
@@ -148,36 +152,55 @@ __device__ __forceinline__ uint64_t global_ns()
 }
 
 // Bounded wait of one warp until prog[nbr[i]] >= need for every i < nn.
-// Gives up (setting kErrTimeout) after ~4 s or 2^26 polls, or as soon as any
-// other block has raised an error.  Returns true if every flag arrived.
+// Gives up (setting kErrTimeout) after wait_ns nanoseconds (default 4 s) or
+// 2^26 polls, or as soon as any other block has raised an error.  Returns
+// true if every flag arrived.
 constexpr uint64_t kWaitNs = 4000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 26;
 
 __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr, int nn, int need,
-                                                int* err)
+                                                int* err, uint64_t wait_ns = kWaitNs)
 {
     const int lane = threadIdx.x & 31;
     bool ok = true;
     if (lane < nn) {
         const int* f = prog + nbr[lane];
-        if (ld_acquire(f) < need) {
+        // poll with relaxed loads (tight for the first polls, then with a short
+        // sleep); the final acquire orders the reads of the neighbour's data
+        if (ld_relaxed(f) < need) {
             const uint64_t t0 = global_ns();
             uint32_t it = 0;
-            while (ld_acquire(f) < need) {
+            while (ld_relaxed(f) < need) {
                 ++it;
                 if ((it & 31u) == 0u) {
                     if (ld_relaxed(err) != 0) { ok = false; break; }
-                    if (global_ns() - t0 > kWaitNs || it > kWaitPolls) {
+                    if (global_ns() - t0 > wait_ns || it > kWaitPolls) {
                         atomicOr(err, kErrTimeout);
                         ok = false;
                         break;
                     }
                 }
-                __nanosleep(20);
+                if (it > 64u) __nanosleep(32);
             }
         }
+        if (ok) (void)ld_acquire(f);
     }
     return __all_sync(0xffffffffu, ok);
+}
+
+// Integer mode estimate of the photon posterior (log-concave in phi): the
+// Gaussian-approximation centre mu (c + s^2) / (mu + s^2), then one Newton
+// step on d/dphi log T_phi ~ (c - phi)/s^2 + log(mu / (phi + 1/2)).  Any
+// estimate gives the same sums (they run outward until the terms vanish);
+// a close one keeps them short.
+__device__ __forceinline__ int photon_mode(float muf, float cf, float isf)
+{
+    float ph = muf * __fdividef(cf * isf + 1.0f, muf * isf + 1.0f);
+    ph = fmaxf(ph, 0.0f);
+    const float f = (cf - ph) * isf + __logf(__fdividef(muf, ph + 0.5f));
+    const float fp = -isf - __fdividef(1.0f, ph + 0.5f);
+    const float phs = fminf(fmaxf(ph - __fdividef(f, fp), 0.0f), 1.0e7f);
+    return __float2int_rn(phs);
 }
 
 // ---------------------------------------------- per-pixel likelihood change
@@ -204,13 +227,7 @@ __device__ __forceinline__ T dl_pixel(T mu, T x, T c, T is2, T beta, bool& bad)
     }
     // mode of the photon posterior: Gaussian-approximation centre, then one
     // Newton step on d/dphi log T_phi ~ (c - phi)/s^2 + log(mu / (phi + 1/2))
-    const float muf = (float)mu, cf = (float)c, isf = (float)is2;
-    float ph = muf * (cf * isf + 1.0f) / (muf * isf + 1.0f);
-    ph = fmaxf(ph, 0.0f);
-    const float f = (cf - ph) * isf + __logf(muf / (ph + 0.5f));
-    const float fp = -isf - 1.0f / (ph + 0.5f);
-    const float phs = fminf(fmaxf(ph - f / fp, 0.0f), 1.0e7f);
-    const int p0 = __float2int_rn(phs);
+    const int p0 = photon_mode((float)mu, (float)c, (float)is2);
     const T fp0 = (T)p0;
 
     const T inv_mu = P::rcp(mu);
@@ -218,16 +235,24 @@ __device__ __forceinline__ T dl_pixel(T mu, T x, T c, T is2, T beta, bool& bad)
     const T r = (T)1 + d;
     const T lmu = P::wlog(mu);
     T B = (T)1, D = (T)0;
-    // upward: T_{phi+1} = T_phi * mu exp((c - phi - 1/2)/s^2) / (phi + 1)
+    // upward: T_{phi+1} = T_phi * mu exp((c - phi - 1/2)/s^2) / (phi + 1);
+    // two terms per pass, one exit test per pass (a term below kEps of the
+    // sum changes nothing)
     {
         T mg = P::wexp(fmin(lmu + (c - fp0 - (T)0.5) * is2, (T)P::kMaxExp));
         T t = (T)1, e = (T)0;
         T fphi = fp0;
-        for (int it = 0; it < 4096; ++it) {
-            fphi += (T)1;
-            t *= mg * P::rcp(fphi);
-            mg *= beta;
+        for (int it = 0; it < 2048; ++it) {
+            const T f1 = mg * P::rcp(fphi + (T)1);
+            const T f2 = mg * beta * P::rcp(fphi + (T)2);
+            fphi += (T)2;
+            mg *= beta * beta;
+            t *= f1;
             e = fma(e, r, d);                 // r^k - 1
+            B += t;
+            D = fma(t, e, D);
+            t *= f2;
+            e = fma(e, r, d);
             B += t;
             D = fma(t, e, D);
             if (t * fmax((T)1, (T)1 + e) < (T)P::kEps * B) break;
@@ -240,17 +265,158 @@ __device__ __forceinline__ T dl_pixel(T mu, T x, T c, T is2, T beta, bool& bad)
         const T di = -d * ri;                // 1/r - 1
         T t = (T)1, e = (T)0;
         T fphi = fp0;
-        for (int phi = p0; phi > 0; --phi) {
-            t *= hq * fphi;
-            hq *= beta;
-            fphi -= (T)1;
+        int phi = p0;
+        for (; phi > 1; phi -= 2) {
+            const T f1 = hq * fphi;
+            const T f2 = hq * beta * (fphi - (T)1);
+            hq *= beta * beta;
+            fphi -= (T)2;
+            t *= f1;
             e = fma(e, ri, di);               // r^-k - 1
+            B += t;
+            D = fma(t, e, D);
+            t *= f2;
+            e = fma(e, ri, di);
             B += t;
             D = fma(t, e, D);
             if (t * fmax((T)1, (T)1 + e) < (T)P::kEps * B) break;
         }
+        if (phi == 1) {                       // odd remainder: the phi = 0 term
+            t *= hq * fphi;
+            e = fma(e, ri, di);
+            B += t;
+            D = fma(t, e, D);
+        }
     }
-    return -x + fp0 * P::log1p(d) + P::log1p(D / B);
+    return -x + fp0 * P::log1p(d) + P::log1p(D * P::rcp(B));
+}
+
+// ------------------------------------------ photon-posterior cumulant cache
+// For the float sweep each camera pixel caches the first six cumulants of
+// its photon-count posterior w_phi ∝ exp(-(c - phi)^2/(2 s^2)) mu^phi / phi!
+// at the current mu, stored as c_j = kappa_j / j! ({c1..c4} and {c5, c6}).
+// Since S(mu e^t)/S(mu) = E_w[e^{t phi}], the change of Eq. 6 for
+// mu -> mu (1 + d) is -mu d + K(t), t = log1p(d), with K the cumulant
+// generating function: K(t) = sum_j c_j t^j.  Window pixels with
+// |d| <= kCumEval use the six-term series (the first omitted term,
+// kappa7 |t|^7 / 7!, stays below ~5e-8 for photon counts up to ~10^2);
+// others use the exact sum (dl_pixel).  When mu changes by an accepted
+// update the cache is moved by exponential tilting (the tilted
+// distribution's cumulants are the derivatives of K at t:
+// c_j' = sum_i C(j+i, i) c_{j+i} t^i) when |d| <= kCumShift, or recomputed
+// exactly; the double refresh rebuilds it from scratch.
+constexpr float kCumEval = 0.15f;
+constexpr float kCumShift = 0.02f;
+
+struct Cum6 {
+    float4 a;   // c1 (mean), c2, c3, c4
+    float2 b;   // c5, c6
+};
+
+// log1p(d): its series to d^5 for |d| <= 0.05 (remainder below d^6/6),
+// the library function beyond
+__device__ __forceinline__ float log1p_small(float d)
+{
+    return d * fmaf(d, fmaf(d, fmaf(d, fmaf(d, 0.2f, -0.25f), 0.33333334f), -0.5f), 1.0f);
+}
+__device__ __forceinline__ float log1p_cum(float d)
+{
+    return fabsf(d) <= 0.05f ? log1p_small(d) : log1pf(d);
+}
+
+// K(t) - x
+__device__ __forceinline__ float cgf_delta(float x, float t, float4 a, float2 b)
+{
+    const float p = fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, b.y, b.x), a.w), a.z), a.y), a.x);
+    return fmaf(t, p, -x);
+}
+
+__device__ __forceinline__ Cum6 cgf_shift(float4 a, float2 b, float t)
+{
+    Cum6 r;
+    r.a.x = fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, 6.0f * b.y, 5.0f * b.x), 4.0f * a.w), 3.0f * a.z), 2.0f * a.y), a.x);
+    r.a.y = fmaf(t, fmaf(t, fmaf(t, fmaf(t, 15.0f * b.y, 10.0f * b.x), 6.0f * a.w), 3.0f * a.z), a.y);
+    r.a.z = fmaf(t, fmaf(t, fmaf(t, 20.0f * b.y, 10.0f * b.x), 4.0f * a.w), a.z);
+    r.a.w = fmaf(t, fmaf(t, 15.0f * b.y, 5.0f * b.x), a.w);
+    r.b.x = fmaf(t, 6.0f * b.y, b.x);
+    r.b.y = b.y;
+    return r;
+}
+
+// Exact cumulants of the photon posterior at mu (same mode estimate and
+// outward recurrences as dl_pixel): raw moments of k = phi - phi0, then
+// central moments about the mean, then cumulants.
+template <typename T>
+__device__ __forceinline__ Cum6 photon_cumulants(T mu, T c, T is2, T beta)
+{
+    using P = Prec<T>;
+    const int p0 = photon_mode((float)mu, (float)c, (float)is2);
+    const T fp0 = (T)p0;
+    const T lmu = P::wlog(mu);
+    T S[7] = {1, 0, 0, 0, 0, 0, 0};
+    {
+        T mg = P::wexp(fmin(lmu + (c - fp0 - (T)0.5) * is2, (T)P::kMaxExp));
+        T t = 1, fphi = fp0, k = 0;
+        for (int it = 0; it < 4096; ++it) {
+            fphi += (T)1;
+            k += (T)1;
+            t *= mg * P::rcp(fphi);
+            mg *= beta;
+            T tk = t;
+#pragma unroll
+            for (int jj = 0; jj < 7; ++jj) {
+                S[jj] += tk;
+                tk *= k;
+            }
+            if (t < (T)P::kEps * (T)0.0625 * S[0]) break;
+        }
+    }
+    if (p0 > 0) {
+        T hq = P::wexp(fmin(-lmu - (c - fp0 + (T)0.5) * is2, (T)P::kMaxExp));
+        T t = 1, fphi = fp0, k = 0;
+        for (int phi = p0; phi > 0; --phi) {
+            t *= hq * fphi;
+            hq *= beta;
+            fphi -= (T)1;
+            k -= (T)1;
+            T tk = t;
+#pragma unroll
+            for (int jj = 0; jj < 7; ++jj) {
+                S[jj] += tk;
+                tk *= k;
+            }
+            if (t < (T)P::kEps * (T)0.0625 * S[0]) break;
+        }
+    }
+    const T i0 = (T)1 / S[0];
+    const T m = S[1] * i0, e2 = S[2] * i0, e3 = S[3] * i0, e4 = S[4] * i0, e5 = S[5] * i0, e6 = S[6] * i0;
+    const T m2 = m * m, m3 = m2 * m, m4 = m3 * m;
+    const T u2 = e2 - m2;
+    const T u3 = e3 - (T)3 * m * e2 + (T)2 * m3;
+    const T u4 = e4 - (T)4 * m * e3 + (T)6 * m2 * e2 - (T)3 * m4;
+    const T u5 = e5 - (T)5 * m * e4 + (T)10 * m2 * e3 - (T)10 * m3 * e2 + (T)4 * m4 * m;
+    const T u6 = e6 - (T)6 * m * e5 + (T)15 * m2 * e4 - (T)20 * m3 * e3 + (T)15 * m4 * e2 - (T)5 * m4 * m2;
+    const T k4 = u4 - (T)3 * u2 * u2;
+    const T k5 = u5 - (T)10 * u3 * u2;
+    const T k6 = u6 - (T)15 * u4 * u2 - (T)10 * u3 * u3 + (T)30 * u2 * u2 * u2;
+    Cum6 r;
+    r.a = make_float4((float)(fp0 + m), (float)(u2 / (T)2), (float)(u3 / (T)6), (float)(k4 / (T)24));
+    r.b = make_float2((float)(k5 / (T)120), (float)(k6 / (T)720));
+    return r;
+}
+
+// Out-of-line copies for the float sweep, where the exact sums are the rare
+// branch: keeping them out of the unrolled window loop keeps register use low.
+__device__ __forceinline__ float dl_pixel_call(float mu, float x, float c, float is2, float beta, int* bad)
+{
+    bool b = false;
+    const float r = dl_pixel<float>(mu, x, c, is2, beta, b);
+    if (b) *bad = 1;
+    return r;
+}
+__device__ __forceinline__ Cum6 photon_cumulants_call(float mu, float c, float is2, float beta)
+{
+    return photon_cumulants<float>(mu, c, is2, beta);
 }
 
 // Full log marginal likelihood of one camera pixel in double (Eq. 6):

@@ -24,6 +24,7 @@ struct Shape {
     int ph, pw, K, nhalf;
     int ent_off;            // first entry in the problem's entry arrays
     int twh_off, tww_off;   // twiddle tables exp(-2 pi i j / ph), exp(-2 pi i j / pw)
+    float inv_ph, inv_pw;   // 1/ph, 1/pw for the small-integer modulo of twiddle indices
 };
 
 // One problem (frame + calibration + PSF), shared by its chains.
@@ -59,12 +60,15 @@ struct Chain {
     void* rho;                       // Ho*Wo, T
     void* mu;                        // H*mu_pitch, T
     void* spec;                      // spec_len complex T
+    float4* cum;                     // H*mu_pitch photon-posterior cumulants c1..c4 (float chains) or null
+    float2* cum2;                    // H*mu_pitch cumulants c5, c6
     double* rho_sum;                 // Ho*Wo
     double* rho_sq;                  // Ho*Wo or null
     double* trace_part;              // [slot][patch] accepted dL + dP
     unsigned long long* acc_count;   // [sweep - 1]
     uint8_t* acc_log;                // [sweep - 1][Ho*Wo] or null
     int* prog;                       // per tile: steps completed in this launch
+    int* acc_step;                   // per tile: last step (1-based) with an accepted update
     double* trace;                   // [sweep 0..max_sweeps]
     int tpi, tpj, nti, ntj;          // tile shape (patches) and tile grid
     int cta_base;                    // first block of this chain in the sweep grid
@@ -78,6 +82,8 @@ struct SweepArgs {
     int n_sweeps;                    // sweeps in this launch
     int* err;
     int resident;                    // 1: tile state (data, spectra, rho) held in shared memory
+    unsigned long long wait_ns;      // limit of each neighbour wait
+    int silent_block;                // test knob: this block never publishes progress (-1: none)
 };
 
 // Threads that cooperate on one pixel update: a function of the PSF side

@@ -226,6 +226,12 @@ __global__ void __launch_bounds__(kRedThreads) k_refresh_mu(Image im, Chain ch, 
         } else {
             const double* d = im.dat64 + 4 * (size_t)idx;
             ll = loglik64(mu, d[0], d[1], d[2], d[3]);
+            if (write && ch.cum) {
+                // the cache describes the stored (rounded) expected image
+                const Cum6 q = photon_cumulants<double>((double)(T)mu, d[0], d[1], d[2]);
+                ch.cum[(size_t)a * im.mu_pitch + b] = q.a;
+                ch.cum2[(size_t)a * im.mu_pitch + b] = q.b;
+            }
         }
         if (write) reinterpret_cast<T*>(ch.mu)[(size_t)a * im.mu_pitch + b] = (T)mu;
     }

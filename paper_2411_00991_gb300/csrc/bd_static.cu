@@ -12,7 +12,7 @@
 #include <cstdio>
 #include <mutex>
 
-#include "../../include/bdecon.h"
+#include "bdecon.h"
 #include "bd_device.cuh"
 
 namespace bd {

@@ -25,6 +25,8 @@
 // In a resident plan the tile's per-pixel data constants (with the PSF halo),
 // patch spectra and object values stay in shared memory for the launch; only
 // mu, shared with the neighbouring tiles, is read from global memory (L2).
+#include <type_traits>
+
 #include "bd_device.cuh"
 
 namespace bd {
@@ -43,32 +45,130 @@ __device__ __forceinline__ void prior_term(T xr, T xi, T wr, T wi, T delta, T wa
     const T n2n = rn * rn + in * in;
     if (!(n2n > (T)0)) bad = true;
     const T mo = P::sqrt(n2), mn = P::sqrt(n2n);
-    accP += wa * P::log1p(dd / n2);
-    accS += mult * (dd / (mn + mo));
+    accP += wa * P::log1p(dd * P::rcp(n2));
+    accS += mult * (dd * P::rcp(mn + mo));
     accA += mult * mo;
+}
+
+// x mod n for 0 <= x < 2^22 through a float reciprocal (exact after one correction)
+__device__ __forceinline__ int small_mod(int x, int n, float inv_n)
+{
+    int r = x - n * __float2int_rz((float)x * inv_n);
+    r += r < 0 ? n : 0;
+    r -= r >= n ? n : 0;
+    return r;
 }
 
 template <typename T>
 __device__ __forceinline__ void twiddle(const T* tw, const Shape& sh, int kl, int u, int v, T& wr, T& wi)
 {
     const int k = kl >> 16, l = kl & 0xffff;
-    const T* eh = tw + 2 * (sh.twh_off + (k * u) % sh.ph);
-    const T* ew = tw + 2 * (sh.tww_off + (l * v) % sh.pw);
+    const T* eh = tw + 2 * (sh.twh_off + small_mod(k * u, sh.ph, sh.inv_ph));
+    const T* ew = tw + 2 * (sh.tww_off + small_mod(l * v, sh.pw, sh.inv_pw));
     wr = eh[0] * ew[0] - eh[1] * ew[1];
     wi = eh[0] * ew[1] + eh[1] * ew[0];
 }
 
 constexpr int kMaxPx = 4;   // window pixels per thread fetched in one batch
 
-template <typename T, bool RES>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
+// a2: the proposal of one update from its Philox counter (m, t, chain, 0):
+// z standard normal (Box-Muller), log u, rho' = rho exp(step z).
+template <typename T>
+__device__ __forceinline__ void proposal(const Image& im, const Chain& ch, int m, int t, T r_old, T& z, T& lu,
+                                         T& r_new, T& delta)
 {
     using P = Prec<T>;
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)t, (uint32_t)ch.chain, 0u), im.seed_lo,
+                                  im.seed_hi);
+    z = P::gauss(uniform23<T>(x.x), uniform23<T>(x.y));
+    lu = P::log(uniform23<T>(x.z));
+    r_new = r_old * P::exp((T)im.step * z);
+    delta = r_new - r_old;
+}
+
+// Likelihood part of one update for one team thread: fetches the expected
+// image (and, for float sweeps, the cached cumulants) of its window pixels
+// in one batch, sums their Eq. 6 changes, and leaves the warp's partial sum
+// and bad flag in out[0..1].  muv keeps the fetched expected image values.
+// Fetch the first batch of a thread's window values (expected image and
+// cached cumulants) so the loads are in flight while other work proceeds.
+template <typename T, bool CUM>
+__device__ __forceinline__ void window_fetch(const T* mu_g, const float4* cum_g, const float2* cum2_g,
+                                             const Image& im, int i, int j, int lt, T (&muv)[kMaxPx],
+                                             float4 (&cq)[kMaxPx], float2 (&cq2)[kMaxPx], int k0)
+{
+    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L, NT = team_threads(L);
+#pragma unroll
+    for (int jj = 0; jj < kMaxPx; ++jj) {
+        const int k = k0 + jj * NT;
+        const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
+        const bool in = k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W;
+        muv[jj] = in ? __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb) : (T)-1;
+        if (CUM) {
+            cq[jj] = in ? __ldcg(cum_g + (size_t)aa * im.mu_pitch + bb) : make_float4(0, 0, 0, 0);
+            cq2[jj] = in ? __ldcg(cum2_g + (size_t)aa * im.mu_pitch + bb) : make_float2(0, 0);
+        }
+    }
+}
+
+template <typename T, bool RES, bool CUM>
+__device__ __forceinline__ void lik_partial(const T* mu_g, const float4* cum_g, const float2* cum2_g, const Dat4<T>* dat_s,
+                                            const Dat4<T>* dat_g, const T* Ks, const Image& im, int i, int j,
+                                            int a_lo, int b_lo, int rw, int lt, int NT, T delta, T (&muv)[kMaxPx],
+                                            T* out, int lane, float4 (&cq)[kMaxPx], float2 (&cq2)[kMaxPx],
+                                            bool prefetched)
+{
+    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L;
+    T accL = 0;
+    bool badL = false;
+    for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
+        if (!(prefetched && k0 == lt)) window_fetch<T, CUM>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, k0);
+#pragma unroll
+        for (int jj = 0; jj < kMaxPx; ++jj) {
+            const int k = k0 + jj * NT;
+            const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
+            if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
+                const T xk = mul_rn(delta, Ks[k]);
+                if (CUM) {
+                    const float d = (float)xk * Prec<float>::rcp((float)muv[jj]);
+                    if (fabsf(d) <= kCumEval) {
+                        accL += (T)cgf_delta((float)xk, log1p_cum(d), cq[jj], cq2[jj]);
+                        continue;
+                    }
+                }
+                const Dat4<T> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
+                if (CUM) {
+                    int b = 0;
+                    accL += (T)dl_pixel_call((float)muv[jj], (float)xk, (float)dv.c, (float)dv.is2, (float)dv.beta,
+                                             &b);
+                    badL = badL || b;
+                } else {
+                    accL += dl_pixel<T>(muv[jj], xk, dv.c, dv.is2, dv.beta, badL);
+                }
+            }
+        }
+    }
+    accL = warp_sum(accL);
+    const bool wb = __any_sync(0xffffffffu, badL);
+    if (lane == 0) {
+        out[0] = accL;
+        out[1] = wb ? (T)1 : (T)0;
+    }
+}
+
+template <typename T, bool RES>
+__global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_sweep(SweepArgs a)
+{
+    using P = Prec<T>;
+    constexpr bool CUM = std::is_same<T, float>::value;   // float sweeps use the cumulant cache
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_nbr[8];
     __shared__ int s_nn;
     __shared__ int s_abort;
     __shared__ int s_ci;
+    __shared__ int s_stale;
+    __shared__ int s_acc_any;
+    __shared__ T s_prop[2][8][4];   // next-step proposals of one-patch teams: z, log u, rho', delta
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -107,6 +207,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
     T* rho_g = reinterpret_cast<T*>(ch.rho);
     T* mu_g = reinterpret_cast<T*>(ch.mu);
     T* spec_g = reinterpret_cast<T*>(ch.spec);
+    float4* cum_g = ch.cum;
+    float2* cum2_g = ch.cum2;
     const Dat4<T>* dat_g = dat<T>(im);
 
     // ---- prologue: neighbours, tables, resident tile state
@@ -119,6 +221,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
             }
         s_nn = nn;
         s_abort = 0;
+        s_stale = 0;
+        s_acc_any = 0;
     }
     for (int k = tid; k < LL; k += blockDim.x) Ks[k] = kern<T>(im)[k];
     for (int k = tid; k < 2 * im.n_tw; k += blockDim.x) tws[k] = twid<T>(im)[k];
@@ -156,6 +260,24 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
     const T step = (T)im.step;
     const int nsteps = a.n_sweeps * S2;
     int n_acc = 0;
+    // with one update per team and step, a warp of the team draws the next
+    // step's proposal ahead of time (before the neighbour wait); not when a
+    // patch has a single class (S = 1), where the next step revisits the pixel
+    const bool ahead = rounds == 1 && S2 > 1;
+    const int pwarp = nwt > 1 ? 1 : 0;   // the drawing warp: not the one that polls the flags
+    if (ahead && in_team && twarp == pwarp && g < npt && nsteps > 0) {
+        const int pi = pi0 + g / tw_, pj = pj0 + (g - (g / tw_) * tw_);
+        const Shape& sh = im.shape[shape_index(im, pi, pj)];
+        if (sh.ph > 0 && sh.pw > 0) {
+            const int m = (pi * S) * im.Wo + pj * S;
+            T z, lu, rn, dl;
+            proposal<T>(im, ch, m, a.t0 + 1, RES ? rho_s[(size_t)g * S2] : rho_g[m], z, lu, rn, dl);
+            if (lane == 0) {
+                s_prop[0][g][0] = z; s_prop[0][g][1] = lu; s_prop[0][g][2] = rn; s_prop[0][g][3] = dl;
+            }
+        }
+    }
+    __syncthreads();
 
     for (int s = 0; s < nsteps; ++s) {
         const int slot = s / S2, c = s - slot * S2;
@@ -177,15 +299,23 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
             T z = 0, lu = 0, r_old = 0, r_new = 0, delta = 0;
             bool badP = false;
             T* spec_p = RES ? spec_s + (size_t)q * 2 * im.max_nhalf : spec_g + 2 * im.patch_off[pi * im.npj + pj];
+            T muv[kMaxPx];
+            float4 cq[kMaxPx];
+            float2 cq2[kMaxPx];
+            // the window's first batch is fetched before the prior work so its
+            // latency overlaps the arithmetic below
+            if (active) window_fetch<T, CUM>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, lt);
             // a2 + a4: proposal and prior change (own tile state only)
             if (active) {
-                const uint4 x = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)t, (uint32_t)ch.chain, 0u),
-                                              im.seed_lo, im.seed_hi);
-                z = P::gauss(uniform23<T>(x.x), uniform23<T>(x.y));
-                lu = P::log(uniform23<T>(x.z));
-                r_old = RES ? rho_s[(size_t)q * S2 + u * S + v] : rho_g[m];
-                r_new = r_old * P::exp(step * z);
-                delta = r_new - r_old;
+                if (ahead) {
+                    z = s_prop[s & 1][g][0];
+                    lu = s_prop[s & 1][g][1];
+                    r_new = s_prop[s & 1][g][2];
+                    delta = s_prop[s & 1][g][3];
+                } else {
+                    r_old = RES ? rho_s[(size_t)q * S2 + u * S + v] : rho_g[m];
+                    proposal<T>(im, ch, m, t, r_old, z, lu, r_new, delta);
+                }
                 T accP = 0, accS = 0, accA = 0;
                 for (int e = lt; e < sh.nhalf; e += NT) {
                     T wr, wi;
@@ -205,60 +335,60 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
                     red1[twarp * 4 + 3] = wb ? (T)1 : (T)0;
                 }
             }
+            // a3: likelihood change over the PSF window.  For the first round of
+            // a step this runs before the neighbour wait, on the expected image
+            // as it is now; it is redone below only if a neighbouring tile
+            // accepted an update since this block last waited for it.
+            if (active)
+                lik_partial<T, RES, CUM>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT, delta,
+                                         muv, red2 + twarp * 4, lane, cq, cq2, true);
+            if (ahead && in_team && twarp == pwarp && q < npt && s + 1 < nsteps) {
+                const int s1 = s + 1, c1 = s1 % S2;
+                const int u1 = c1 / S, v1 = c1 - (c1 / S) * S;
+                const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
+                const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
+                if (u1 < sh1.ph && v1 < sh1.pw) {
+                    const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
+                    T z1, lu1, rn1, dl1;
+                    proposal<T>(im, ch, m1, a.t0 + 1 + s1 / S2, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1],
+                                z1, lu1, rn1, dl1);
+                    if (lane == 0) {
+                        s_prop[s1 & 1][g][0] = z1; s_prop[s1 & 1][g][1] = lu1;
+                        s_prop[s1 & 1][g][2] = rn1; s_prop[s1 & 1][g][3] = dl1;
+                    }
+                }
+            }
             if (r == 0 && s > 0 && tid < 32) {
-                const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err);
-                if (lane == 0 && !ok) s_abort = 1;
+                bool stale = false;
+                const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns);
+                if (ok && lane < s_nn) stale = ld_relaxed(ch.acc_step + s_nbr[lane]) >= s;
+                stale = __any_sync(0xffffffffu, stale);
+                if (lane == 0) {
+                    if (!ok) s_abort = 1;
+                    s_stale = stale ? 1 : 0;
+                }
             }
             __syncthreads();
             if (s_abort) return;
-            // a3: likelihood change over the PSF window
-            T muv[kMaxPx];
-            T dP = 0;
-            bool bad = false;
+            if (r == 0 && s > 0 && s_stale) {
+                if (active)
+                    lik_partial<T, RES, CUM>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT, delta,
+                                             muv, red2 + twarp * 4, lane, cq, cq2, false);
+                __syncthreads();
+            }
+            // a5: Metropolis-Hastings decision with the Hastings term of the log-space walk
             if (active) {
-                T sP = 0, sS = 0, sA = 0;
+                T sP = 0, sS = 0, sA = 0, dL = 0;
+                bool bad = false;
                 for (int w = 0; w < nwt; ++w) {
                     sP += red1[w * 4 + 0];
                     sS += red1[w * 4 + 1];
                     sA += red1[w * 4 + 2];
                     bad = bad || red1[w * 4 + 3] != (T)0;
-                }
-                dP = sP + (T)(sh.K - 1) * P::log1p(sS / sA);
-                T accL = 0;
-                bool badL = false;
-                for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
-#pragma unroll
-                    for (int jj = 0; jj < kMaxPx; ++jj) {
-                        const int k = k0 + jj * NT;
-                        const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
-                        muv[jj] = (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W)
-                                      ? __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb) : (T)-1;
-                    }
-#pragma unroll
-                    for (int jj = 0; jj < kMaxPx; ++jj) {
-                        const int k = k0 + jj * NT;
-                        const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
-                        if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
-                            const Dat4<T> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
-                            accL += dl_pixel<T>(muv[jj], mul_rn(delta, Ks[k]), dv.c, dv.is2, dv.beta, badL);
-                        }
-                    }
-                }
-                accL = warp_sum(accL);
-                const bool wb = __any_sync(0xffffffffu, badL);
-                if (lane == 0) {
-                    red2[twarp * 4 + 0] = accL;
-                    red2[twarp * 4 + 1] = wb ? (T)1 : (T)0;
-                }
-            }
-            __syncthreads();
-            // a5: Metropolis-Hastings decision with the Hastings term of the log-space walk
-            if (active) {
-                T dL = 0;
-                for (int w = 0; w < nwt; ++w) {
                     dL += red2[w * 4 + 0];
                     bad = bad || red2[w * 4 + 1] != (T)0;
                 }
+                const T dP = sP + (T)(sh.K - 1) * P::log1p(sS / sA);
                 const bool accept = !bad && (lu < dL + dP + step * z);
                 if (accept) {
                     const bool one_batch = LL <= NT * kMaxPx;
@@ -270,8 +400,24 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
                             if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
                                 // same value the proposal was scored with: still in registers when
                                 // the window took one batch, else reloaded (unchanged since)
-                                const T old = one_batch ? muv[jj] : __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb);
-                                __stcg(mu_g + (size_t)aa * im.mu_pitch + bb, add_rn(old, mul_rn(delta, Ks[k])));
+                                const size_t idx = (size_t)aa * im.mu_pitch + bb;
+                                const T old = one_batch ? muv[jj] : __ldcg(mu_g + idx);
+                                const T xk = mul_rn(delta, Ks[k]);
+                                const T nmu = add_rn(old, xk);
+                                __stcg(mu_g + idx, nmu);
+                                if (CUM) {
+                                    const float d = (float)xk * Prec<float>::rcp((float)old);
+                                    Cum6 nq;
+                                    if (fabsf(d) <= kCumShift) {
+                                        nq = cgf_shift(__ldcg(cum_g + idx), __ldcg(cum2_g + idx), log1p_small(d));
+                                    } else {
+                                        const Dat4<T> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
+                                        nq = photon_cumulants_call((float)nmu, (float)dv.c, (float)dv.is2,
+                                                                   (float)dv.beta);
+                                    }
+                                    __stcg(cum_g + idx, nq.a);
+                                    __stcg(cum2_g + idx, nq.b);
+                                }
                             }
                         }
                     }
@@ -286,6 +432,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
                         rho_g[m] = r_new;
                         ch.trace_part[(size_t)slot * im.n_patches + pi * im.npj + pj] += (double)dL + (double)dP;
                         ++n_acc;
+                        s_acc_any = 1;
                     }
                 }
                 if (ch.acc_log != nullptr && lt == 0) ch.acc_log[(size_t)(t - 1) * im.Ho * im.Wo + m] = accept ? 1 : 0;
@@ -311,9 +458,19 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a)
             n_acc = 0;
             __syncthreads();
         }
-        if (tid == 0) {
-            __threadfence();
-            st_release(ch.prog + tl, s + 1);
+        if (tid == 0 && (int)blockIdx.x != a.silent_block) {
+            // publish: the last step with an accepted update (read by the
+            // neighbours' staleness check), then the step count (release)
+            // (a step without an accepted update wrote nothing the neighbours
+            // read, and its own reads were consumed before the barrier, so a
+            // plain store suffices; otherwise release the mu writes)
+            if (s_acc_any) {
+                ch.acc_step[tl] = s + 1;
+                s_acc_any = 0;
+                st_release(ch.prog + tl, s + 1);
+            } else {
+                st_relaxed(ch.prog + tl, s + 1);
+            }
         }
     }
     // ---- epilogue: resident spectra back to global memory
@@ -394,8 +551,17 @@ __global__ void __launch_bounds__(256) k_delta(const Image* imp, const Chain* ch
             const int k = k0 + jj * NT;
             const int aa = i - 2 * R + k / L, bb = j - 2 * R + k % L;
             if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
+                const size_t idx = (size_t)aa * im.mu_pitch + bb;
+                const T xk = mul_rn(delta, K[k]);
+                if (std::is_same<T, float>::value && ch.cum) {
+                    const float d = (float)xk * Prec<float>::rcp((float)mu[idx]);
+                    if (fabsf(d) <= kCumEval) {
+                        accL += (T)cgf_delta((float)xk, log1p_cum(d), ch.cum[idx], ch.cum2[idx]);
+                        continue;
+                    }
+                }
                 const Dat4<T> dv = dt[(size_t)aa * W + bb];
-                accL += dl_pixel<T>(mu[(size_t)aa * im.mu_pitch + bb], mul_rn(delta, K[k]), dv.c, dv.is2, dv.beta, badL);
+                accL += dl_pixel<T>(mu[idx], xk, dv.c, dv.is2, dv.beta, badL);
             }
         }
     accP = warp_sum(accP);

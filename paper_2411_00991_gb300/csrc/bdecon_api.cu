@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/bdecon.h"
+#include "bdecon.h"
 #include "bd_internal.h"
 
 using namespace bd;
@@ -44,7 +44,7 @@ struct ProbHost {
 };
 
 struct ChainHost {
-    size_t o_rho, o_mu, o_spec, o_tpart, o_acc, o_log, o_prog, o_trace;
+    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace;
 };
 
 }  // namespace
@@ -78,6 +78,8 @@ struct bdecon_handle {
     double* d_up = nullptr;         // staging buffer for set_state / results
     int64_t launches = 0;
     bool timing = false;
+    int silent_block = -1;              // test knob (bdecon_set_fault)
+    unsigned long long wait_ns = 4000000000ull;
     std::vector<cudaEvent_t> ev_pool;    // pairs (start, stop), reused
     size_t ev_used = 0;
     std::string err;
@@ -198,6 +200,8 @@ void describe(ProbHost& ph)
         ph.max_nhalf = std::max(ph.max_nhalf, sh.nhalf);
         sh.twh_off = twoff; twoff += sh.ph;
         sh.tww_off = twoff; twoff += sh.pw;
+        sh.inv_ph = 1.0f / (float)sh.ph;
+        sh.inv_pw = 1.0f / (float)sh.pw;
     }
     ph.n_tw = twoff;
     ph.patch_off.resize(ph.n_patches);
@@ -338,10 +342,13 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
             x.o_rho = A.take(ts * nobj);
             x.o_mu = A.take(ts * (size_t)ph.H * ph.pitch);
             x.o_spec = A.take(2 * ts * (size_t)ph.spec_len);
+            x.o_cum = prec == BDECON_FP32 ? A.take(16 * (size_t)ph.H * ph.pitch) : 0;
+            x.o_cum2 = prec == BDECON_FP32 ? A.take(8 * (size_t)ph.H * ph.pitch) : 0;
             x.o_tpart = A.take(8 * (size_t)kMaxSlots * ph.n_patches);
             x.o_acc = A.take(8 * (size_t)max_sweeps);
             x.o_log = (ph.p.flags & BDECON_FLAG_ACCEPT_LOG) ? A.take((size_t)max_sweeps * nobj) : 0;
             x.o_prog = A.take(4 * (size_t)ph.n_patches);
+            x.o_astep = A.take(4 * (size_t)ph.n_patches);
             x.o_trace = A.take(8 * ((size_t)max_sweeps + 1));
             chh.push_back(x);
         }
@@ -474,12 +481,15 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
             const size_t nobj = (size_t)ph.Ho * ph.Wo;
             ch.img = k; ch.chain = c;
             ch.rho = A + x.o_rho; ch.mu = A + x.o_mu; ch.spec = A + x.o_spec;
+            ch.cum = x.o_cum ? (float4*)(A + x.o_cum) : nullptr;
+            ch.cum2 = x.o_cum2 ? (float2*)(A + x.o_cum2) : nullptr;
             ch.rho_sum = (double*)(A + ph.o_sum) + c * nobj;
             ch.rho_sq = ph.o_sq ? (double*)(A + ph.o_sq) + c * nobj : nullptr;
             ch.trace_part = (double*)(A + x.o_tpart);
             ch.acc_count = (unsigned long long*)(A + x.o_acc);
             ch.acc_log = x.o_log ? (uint8_t*)(A + x.o_log) : nullptr;
             ch.prog = (int*)(A + x.o_prog);
+            ch.acc_step = (int*)(A + x.o_astep);
             ch.trace = (double*)(A + x.o_trace);
         }
     }
@@ -615,10 +625,12 @@ bdecon_status bdecon_sweep(bdecon_handle* h, int32_t n)
             const ProbHost& ph = h->probs[ch.img];
             CK(h, cudaMemsetAsync(ch.trace_part, 0, 8 * (size_t)len * ph.n_patches, h->st));
             CK(h, cudaMemsetAsync(ch.prog, 0, 4 * (size_t)ph.n_patches, h->st));
+            CK(h, cudaMemsetAsync(ch.acc_step, 0, 4 * (size_t)ph.n_patches, h->st));
         }
         SweepArgs a;
         a.imgs = h->d_imgs; a.chains = h->d_chains; a.n_chains = (int)h->chains.size();
         a.t0 = t0; a.n_sweeps = len; a.err = h->d_err; a.resident = h->resident;
+        a.wait_ns = h->wait_ns; a.silent_block = h->silent_block;
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (h->timing) {
             if (h->ev_used + 2 > h->ev_pool.size()) {
@@ -878,6 +890,16 @@ bdecon_status bdecon_launch_count(const bdecon_handle* h, int64_t* launches)
 {
     if (!h || !launches) return fail(nullptr, BDECON_ERR_INVALID, "bad arguments");
     *launches = h->launches;
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_set_fault(bdecon_handle* h, int32_t silent_block, int64_t wait_ns)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    if (silent_block >= h->grid) return fail(h, BDECON_ERR_INVALID, "block %d out of range", silent_block);
+    if (wait_ns < 1000000 || wait_ns > 60000000000ll) return fail(h, BDECON_ERR_INVALID, "wait limit out of range");
+    h->silent_block = silent_block < 0 ? -1 : silent_block;
+    h->wait_ns = (unsigned long long)wait_ns;
     return BDECON_OK;
 }
 

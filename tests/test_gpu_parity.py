@@ -222,3 +222,68 @@ def test_accumulated_mean_and_variance():
     np.testing.assert_allclose(var, x.var(axis=0), rtol=1e-8, atol=1e-12)
     R = prob.L // 2
     np.testing.assert_array_equal(crop, mean[R:-R, R:-R])
+
+
+def test_fp32_cumulant_cache_tracks_exact_after_sweeps():
+    # the float sweep scores most window pixels from cached photon-posterior
+    # cumulants that are tilted after each accepted update, and keeps mu and
+    # the patch spectra by float increments; after many sweeps without a
+    # refresh its dL and dP are compared with the double kernel's at the same
+    # (float) state.  Errors of 1e-3 in a log acceptance ratio move the
+    # acceptance probability by 0.1%: far below the Monte Carlo error.
+    prob = synth.small_problem(H=30, W=28, L=7, maps=True, seed=41, refresh_every=0)
+    s = bdecon.Sampler(prob, precision=bdecon.BDECON_FP32, max_sweeps=64)
+    s.sweep(40)
+    rho, _ = s.get_state()
+    assert s.accept_counts().sum() > 0
+    e = bdecon.Sampler(prob, precision=bdecon.BDECON_FP64, max_sweeps=4)
+    e.set_state(rho, 0)
+    Ho, Wo = prob.object_shape()
+    rng = np.random.default_rng(9)
+    errs = []
+    for m in list(rng.integers(0, Ho * Wo, 24)) + [(Ho // 2) * Wo + Wo // 2]:
+        new = float(np.float32(rho.flat[m] * math.exp(rng.normal(0, 0.2))))
+        ok, dl, dp = s.delta(int(m), new)
+        ok64, dl64, dp64 = e.delta(int(m), new)
+        assert ok and ok64
+        errs.append((abs(dl - dl64), abs(dp - dp64), abs(dl64), abs(dp64)))
+    err = np.array(errs)
+    print("max |dL err| %.3g  max |dP err| %.3g" % (err[:, 0].max(), err[:, 1].max()))
+    assert (err[:, 0] <= 1e-3 + 1e-5 * err[:, 2]).all()
+    assert (err[:, 1] <= 1e-3 + 1e-4 * err[:, 3]).all()
+    s.close()
+    e.close()
+
+
+def test_wait_timeout_is_reported_and_context_survives():
+    # a block that never publishes its progress (a flag nothing sets): its
+    # neighbours' bounded waits run out, the device error flag is raised, every
+    # block returns, and the host reads BDECON_ERR_TIMEOUT; no GPU fault
+    prob = synth.small_problem(H=20, W=20, L=5, seed=51)
+    s = bdecon.Sampler(prob, precision=bdecon.BDECON_FP32, max_sweeps=16)
+    s.set_fault(3, 200_000_000)
+    s.sweep(2)
+    with pytest.raises(bdecon.BdeconError) as ei:
+        s.sync()
+    assert ei.value.status == 4
+    with pytest.raises(bdecon.BdeconError) as ei:
+        s.sweep(1)
+    assert ei.value.status == 5
+    s.close()
+    t = bdecon.Sampler(prob, precision=bdecon.BDECON_FP32, max_sweeps=16)
+    t.sweep(3)
+    t.sync()
+    assert np.isfinite(t.trace()).all()
+    t.close()
+
+
+def test_non_finite_expected_image_is_reported():
+    # an object that overflows float gives an infinite expected image: the
+    # refresh raises the numeric flag, read on the host as BDECON_ERR_NUMERIC
+    prob = synth.small_problem(H=12, W=12, L=3, seed=52)
+    s = bdecon.Sampler(prob, precision=bdecon.BDECON_FP32, max_sweeps=8)
+    rho = np.full(prob.object_shape(), 1e300)
+    with pytest.raises(bdecon.BdeconError) as ei:
+        s.set_state(rho, 0)
+    assert ei.value.status == 6
+    s.close()
