@@ -172,6 +172,37 @@ def flops_per_update(prob, mu):
     return L * L * (6 * nterms + 40) + nhalf * 22, nterms
 
 
+# ---------------------------------------------------------- batched form --
+def run_batched(stream, sweeps=2, warm=1, n_images=64):
+    """The batched float form: 64 uneven frames (sides 128..1024, PSF sigma
+    1..4 px, support 2 ceil(3 sigma)+1) x 4 chains in one handle; one
+    cooperative launch per PSF side and sweep segment."""
+    import torch
+    from paper_2411_00991_gb300 import bdecon
+    probs = synth.batch_uneven(n_images)
+    for q in probs:
+        q.burn_in = 0
+        q.refresh_every = 50
+    upd = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * q.n_chains for q in probs)
+    s = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=warm + sweeps + 4, stream=stream)
+    s.sweep(warm)
+    s.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = s.launch_count()
+    e0.record()
+    s.sweep(sweeps)
+    e1.record()
+    torch.cuda.synchronize()
+    s.sync()
+    ms = e0.elapsed_time(e1)
+    groups = len({(q.L, q.n_chains * ((q.H + 2 * q.R + q.L - 1) // q.L) * ((q.W + 2 * q.R + q.L - 1) // q.L) >= 2048) for q in probs})
+    out = dict(value=upd * sweeps / (ms / 1e3), unit="pixel-updates/s", images=len(probs),
+               chains=sum(q.n_chains for q in probs), updates_per_sweep=upd, sweeps=sweeps,
+               ms_per_sweep=ms / sweeps, launch_groups=groups, gpu_launches=s.launch_count() - n0)
+    s.close()
+    return out
+
+
 # ---------------------------------------------------------------- our arm --
 def run_ours(args):
     import torch
@@ -275,6 +306,10 @@ def run_ours(args):
         e2e = dict(value=upd_per_step / dt, unit="pixel-updates/s", h2d_bytes_per_step=int(h2d),
                    d2h_bytes_per_step=int(d2h), ms_per_step=dt * 1e3)
 
+    batched = None
+    if rank == 0 and not args.no_batch:
+        batched = run_batched(stream.cuda_stream)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -322,6 +357,7 @@ def run_ours(args):
                         "frac": ach_gbs / peaks["hbm_gbs"], "bytes_per_update": alg_bytes_per_update,
                         "peak_source": peaks["source"]},
         "fp64": fp64,
+        "batched": batched,
         "acceptance": float(acc[-K * S:].sum() / (K * S * Ho * Wo)),
         "trace_last": float(tr[-1]),
     }
@@ -398,6 +434,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--fp64-sweeps", type=int, default=20)
     ap.add_argument("--profile", type=int, default=0, help="ncu mode: one launch of this many sweeps")
     ap.add_argument("--profile-fp64", action="store_true")

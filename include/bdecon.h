@@ -92,6 +92,12 @@ typedef struct {
     int32_t precision;         /* bdecon_precision                                  */
     int32_t max_sweeps;        /* capacity of the per-sweep trace; 0 -> 4096        */
     int32_t flags;             /* BDECON_FLAG_*                                     */
+    int32_t team_warps;        /* warps cooperating on one pixel update, 1..8; 0 ->
+                                  automatic from the problem alone (1 warp when
+                                  n_chains x patches >= 2048, else one warp per 100
+                                  PSF-window pixels).  It fixes the order of the
+                                  per-update float reductions, so a problem gives
+                                  the same chain alone or in any batch and plan.  */
 } bdecon_problem;
 
 #define BDECON_FLAG_ACCEPT_LOG 1   /* keep the accept decision of every update of

@@ -39,7 +39,8 @@ class _Problem(C.Structure):
                 ("var_map", C.c_void_p), ("read_var", C.c_double),
                 ("stride", C.c_int32), ("n_chains", C.c_int32), ("seed", C.c_uint64),
                 ("step", C.c_double), ("burn_in", C.c_int32), ("refresh_every", C.c_int32),
-                ("precision", C.c_int32), ("max_sweeps", C.c_int32), ("flags", C.c_int32)]
+                ("precision", C.c_int32), ("max_sweeps", C.c_int32), ("flags", C.c_int32),
+                ("team_warps", C.c_int32)]
 
 
 EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bdecon_create_in",
@@ -167,7 +168,7 @@ class Sampler:
             arr[k] = _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
                               int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
                               int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
-                              int(flags))
+                              int(flags), int(getattr(pr, "team_warps", 0)))
         self._arr = arr
         self.precision = precision
         h = C.c_void_p()
@@ -200,7 +201,7 @@ class Sampler:
             arr[k] = _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
                               int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
                               int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
-                              int(flags))
+                              int(flags), int(getattr(pr, "team_warps", 0)))
         n = C.c_size_t()
         s = L.bdecon_workspace_size(arr, len(problems), C.byref(n))
         if s != 0:

@@ -52,6 +52,7 @@ struct Image {
     const int64_t* patch_off;        // offset (complex elements) of each patch's half spectrum
     int64_t spec_len;                // complex elements per chain
     int n_ent, n_tw, max_nhalf;      // table sizes (all shapes)
+    int team;                        // threads per pixel update (a property of the problem)
 };
 
 // One chain (an instance of a problem with its own state and random stream).
@@ -86,15 +87,27 @@ struct SweepArgs {
     int silent_block;                // test knob: this block never publishes progress (-1: none)
 };
 
-// Threads that cooperate on one pixel update: a function of the PSF side
-// only, so each update's arithmetic and reduction order never depend on the
-// launch plan.  One warp per 100 window pixels, 1..8 warps (at most 4
-// window pixels per thread up to L = 32).
+// Threads that cooperate on one pixel update, sized by the PSF side: one warp
+// per 100 window pixels, 1..8 warps (at most 4 window pixels per thread up to
+// L = 32).  The team of a problem is fixed by the problem alone (see
+// problem_team), so its arithmetic and reduction order never depend on the
+// launch plan or on the other problems of a batch.
 __host__ __device__ inline int team_threads(int L)
 {
     int w = (L * L + 99) / 100;
     w = w < 1 ? 1 : (w > 8 ? 8 : w);
     return 32 * w;
+}
+
+// Team of a problem: the requested warps, else one warp when the problem
+// alone has many independent updates per class step (chains x patches >=
+// 2048: throughput comes from many updates in flight), else team_threads(L)
+// (few updates per step: latency comes from the length of each update).
+__host__ __device__ inline int problem_team(int L, int n_chains, int n_patches, int team_warps)
+{
+    if (team_warps > 0) return 32 * (team_warps > 8 ? 8 : team_warps);
+    if ((long long)n_chains * n_patches >= 2048) return 32;
+    return team_threads(L);
 }
 
 // Dynamic shared memory of one sweep block: fixed tables, reduction scratch
@@ -142,10 +155,13 @@ template <typename T>
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 template <typename T>
 int sweep_blocks_per_sm(int threads, size_t smem);
+// zero every chain's progress words, last-accept words and trace partials
+void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_slots, cudaStream_t st,
+                  int64_t* launches);
 void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int t0, int n_sweeps,
                   cudaStream_t st, int64_t* launches);
 template <typename T>
-void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3, int L,
+void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3, int team,
                   cudaStream_t st, int64_t* launches);
 template <typename T>
 void launch_convert(const void* src, double* dst, int64_t n, int rows, int cols, int src_pitch,

@@ -310,6 +310,25 @@ void launch_refresh(const Image& im, const Chain& ch, double* scratch, int write
 template void launch_refresh<float>(const Image&, const Chain&, double*, int, double*, int*, cudaStream_t, int64_t*);
 template void launch_refresh<double>(const Image&, const Chain&, double*, int, double*, int*, cudaStream_t, int64_t*);
 
+// ------------------------------------------------------------ reset -----
+__global__ void k_reset(const Image* imgs, const Chain* chains, int n_slots)
+{
+    const Chain& ch = chains[blockIdx.x];
+    const int np = imgs[ch.img].n_patches;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        ch.prog[k] = 0;
+        ch.acc_step[k] = 0;
+    }
+    for (int k = threadIdx.x; k < n_slots * np; k += blockDim.x) ch.trace_part[k] = 0.0;
+}
+
+void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_slots, cudaStream_t st,
+                  int64_t* launches)
+{
+    k_reset<<<n_chains, 256, 0, st>>>(d_imgs, d_chains, n_slots);
+    ++*launches;
+}
+
 // ------------------------------------------------------------ trace -----
 // trace[t0 + s + 1] = trace[t0] + sum_{s' <= s} sum_p part[s'][p]: the double
 // running sum of accepted dL + dP, per chain (one block per chain).

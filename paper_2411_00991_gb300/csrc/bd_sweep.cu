@@ -11,7 +11,7 @@
 // have finished step s, so every update sees exactly the state the
 // sequential raster scan would give it; there is no grid-wide barrier.
 //
-// Each update is done by a team of team_threads(L) threads with a fixed
+// Each update is done by a team of im.team threads (fixed by the problem) with a fixed
 // assignment of window pixels and spectrum entries and a fixed reduction
 // tree, so results are bit-identical for every launch plan:
 //   a2  Philox4x32-10 counter (m, t, chain, 0) -> z, u; rho' = rho e^{step z}
@@ -97,7 +97,7 @@ __device__ __forceinline__ void window_fetch(const T* mu_g, const float4* cum_g,
                                              const Image& im, int i, int j, int lt, T (&muv)[kMaxPx],
                                              float4 (&cq)[kMaxPx], float2 (&cq2)[kMaxPx], int k0)
 {
-    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L, NT = team_threads(L);
+    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L, NT = im.team;
 #pragma unroll
     for (int jj = 0; jj < kMaxPx; ++jj) {
         const int k = k0 + jj * NT;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     }
     __syncthreads();
 
-    const int NT = team_threads(L);
+    const int NT = im.team;
     const int n_sub = max(1, (int)blockDim.x / NT);
     const int g = tid / NT, lt = tid - (tid / NT) * NT;
     const bool in_team = g < n_sub;
@@ -525,7 +525,7 @@ __global__ void __launch_bounds__(256) k_delta(const Image* imp, const Chain* ch
     const Image& im = *imp;
     const Chain& ch = *chp;
     const int lt = threadIdx.x, lane = lt & 31, twarp = lt >> 5;
-    const int NT = team_threads(im.L), nwt = NT >> 5;
+    const int NT = im.team, nwt = NT >> 5;
     const int i = (int)(m / im.Wo), j = (int)(m % im.Wo);
     const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L;
     const int pi = i / S, pj = j / S, u = i - pi * S, v = j - pj * S;
@@ -593,10 +593,10 @@ __global__ void __launch_bounds__(256) k_delta(const Image* imp, const Chain* ch
 }
 
 template <typename T>
-void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3, int L,
+void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3, int team,
                   cudaStream_t st, int64_t* launches)
 {
-    k_delta<T><<<1, team_threads(L), 0, st>>>(d_im, d_ch, m, rho_new, out3);
+    k_delta<T><<<1, team, 0, st>>>(d_im, d_ch, m, rho_new, out3);
     ++*launches;
 }
 template void launch_delta<float>(const Image*, const Chain*, int64_t, double, double*, int, cudaStream_t, int64_t*);

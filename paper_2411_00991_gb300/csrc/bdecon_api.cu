@@ -43,6 +43,19 @@ struct ProbHost {
     int chain0;
 };
 
+// Problems with the same PSF side, stride and update team share a launch:
+// they have the same number of class steps per sweep and the same block.
+struct Group {
+    std::vector<int> probs;
+    int L = 0, S = 0, team = 32;
+    int threads = 32, warps = 1;
+    bool user_warps = false;
+    int grid = 0;
+    size_t smem = 0;
+    int resident = 1;
+    int chain_off = 0, n_chains = 0;   // slice of the group-ordered chain table
+};
+
 struct ChainHost {
     size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace;
 };
@@ -57,12 +70,10 @@ struct bdecon_handle {
     int precision = 1;
     int max_sweeps = 4096;
     int64_t sweeps = 0;
-    int warps = 1;
-    bool user_warps = false;
-    int grid = 0;
-    int threads = 32;
-    size_t smem = 0;
-    int resident = 1;
+    std::vector<Group> groups;
+    std::vector<int> prob_group;        // problem -> group
+    size_t o_gchains = 0;
+    Chain* d_gchains = nullptr;          // chain descriptors in group order
     bool failed = false;
     int sms = 0;
     cudaStream_t st = nullptr;
@@ -130,6 +141,7 @@ bdecon_status validate(const bdecon_problem& p, int idx)
     if (S < p.L || S > kMaxS)
         return fail(nullptr, BDECON_ERR_INVALID, "problem %d: stride %d must be in [L=%d, %d]", idx, S, p.L, kMaxS);
     if (p.n_chains < 1 || p.n_chains > 4096) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: n_chains %d", idx, p.n_chains);
+    if (p.team_warps < 0 || p.team_warps > 8) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: team_warps %d", idx, p.team_warps);
     if (p.precision != BDECON_FP32 && p.precision != BDECON_FP64)
         return fail(nullptr, BDECON_ERR_INVALID, "problem %d: precision %d", idx, p.precision);
     if (p.burn_in < 0 || p.refresh_every < 0 || p.max_sweeps < 0)
@@ -227,11 +239,12 @@ int occupancy(int prec, int threads, size_t smem)
 
 constexpr size_t kMaxSmem = 227 * 1024;
 
-size_t plan_smem(const bdecon_handle* h, int resident)
+size_t plan_smem(const bdecon_handle* h, const Group& g, int resident)
 {
     const int ts = h->precision == BDECON_FP32 ? 4 : 8;
     size_t mx = 0;
-    for (const auto& ph : h->probs) {
+    for (int k : g.probs) {
+        const ProbHost& ph = h->probs[k];
         const SmemPlan sp = smem_plan(ph.L, ph.S, ph.n_tw, (int)ph.ent_kl.size(), ph.max_nhalf, ph.tpi, ph.tpj,
                                       resident, ts);
         mx = std::max(mx, sp.total);
@@ -239,14 +252,14 @@ size_t plan_smem(const bdecon_handle* h, int resident)
     return mx;
 }
 
-// Grow the tile of the problem with the most blocks; false if none can grow.
-bool grow_worst(bdecon_handle* h)
+// Grow the tile of the group's problem with the most blocks; false if none can grow.
+bool grow_worst(bdecon_handle* h, const Group& g)
 {
     int worst = -1, wb = -1;
-    for (size_t k = 0; k < h->probs.size(); ++k) {
+    for (int k : g.probs) {
         const ProbHost& ph = h->probs[k];
         const int b = blocks_of(ph);
-        if (!ph.user_plan && !(ph.tpi >= ph.npi && ph.tpj >= ph.npj) && b > wb) { wb = b; worst = (int)k; }
+        if (!ph.user_plan && !(ph.tpi >= ph.npi && ph.tpj >= ph.npj) && b > wb) { wb = b; worst = k; }
     }
     if (worst < 0) return false;
     ProbHost& ph = h->probs[worst];
@@ -254,46 +267,46 @@ bool grow_worst(bdecon_handle* h)
     return true;
 }
 
-// Launch plan: block = the largest update team of the batch (or the user's
-// warps); tiles grow from one patch until every block of every chain is
-// co-resident.  Resident plans (tile state in shared memory) are preferred;
-// if none fits, tile state is streamed from global memory.
-bdecon_status make_plan(bdecon_handle* h)
+// Launch plan of one group: block = the update team of its PSF side (or the
+// user's warps); tiles grow from one patch until every block of every chain
+// of the group is co-resident.  Resident plans (tile state in shared memory)
+// are preferred; if none fits, tile state is streamed from global memory.
+bdecon_status plan_group(bdecon_handle* h, Group& g)
 {
     int team = 32;
-    for (const auto& ph : h->probs) team = std::max(team, team_threads(ph.L));
-    h->threads = h->user_warps ? std::max(32 * h->warps, team) : team;
-    h->warps = h->threads / 32;
+    for (int k : g.probs) team = std::max(team, h->imgs[k].team);
+    g.threads = g.user_warps ? std::max(32 * g.warps, team) : team;
+    g.warps = g.threads / 32;
     bool done = false;
     for (int resident = 1; resident >= 0 && !done; --resident) {
-        for (auto& ph : h->probs)
-            if (!ph.user_plan) ph.tpi = ph.tpj = 1;
+        for (int k : g.probs)
+            if (!h->probs[k].user_plan) h->probs[k].tpi = h->probs[k].tpj = 1;
         for (;;) {
-            const size_t smem = plan_smem(h, resident);
+            const size_t smem = plan_smem(h, g, resident);
             int tot = 0;
-            for (const auto& ph : h->probs) tot += blocks_of(ph);
+            for (int k : g.probs) tot += blocks_of(h->probs[k]);
             if (smem <= kMaxSmem) {
-                const int bps = occupancy(h->precision, h->threads, smem);
+                const int bps = occupancy(h->precision, g.threads, smem);
                 if (bps > 0 && tot <= bps * h->sms) {
-                    h->smem = smem;
-                    h->resident = resident;
+                    g.smem = smem;
+                    g.resident = resident;
                     done = true;
                     break;
                 }
             } else if (resident) {
                 break;   // tiles only grow: resident state will not fit
             }
-            if (!grow_worst(h)) break;
+            if (!grow_worst(h, g)) break;
         }
     }
     if (!done) {
         int tot = 0;
-        for (const auto& ph : h->probs) tot += blocks_of(ph);
+        for (int k : g.probs) tot += blocks_of(h->probs[k]);
         return fail(h, BDECON_ERR_INVALID, "no launch plan: %d blocks of %d threads cannot all be co-resident", tot,
-                    h->threads);
+                    g.threads);
     }
     int base = 0;
-    for (size_t k = 0; k < h->probs.size(); ++k) {
+    for (int k : g.probs) {
         ProbHost& ph = h->probs[k];
         const int nti = (ph.npi + ph.tpi - 1) / ph.tpi, ntj = (ph.npj + ph.tpj - 1) / ph.tpj;
         for (int c = 0; c < ph.p.n_chains; ++c) {
@@ -303,8 +316,25 @@ bdecon_status make_plan(bdecon_handle* h)
             base += nti * ntj;
         }
     }
-    h->grid = base;
+    g.grid = base;
+    return BDECON_OK;
+}
+
+bdecon_status make_plan(bdecon_handle* h)
+{
+    std::vector<Chain> gch;
+    for (auto& g : h->groups) {
+        bdecon_status s = plan_group(h, g);
+        if (s != BDECON_OK) return s;
+        g.chain_off = (int)gch.size();
+        for (int k : g.probs) {
+            const ProbHost& ph = h->probs[k];
+            for (int c = 0; c < ph.p.n_chains; ++c) gch.push_back(h->chains[ph.chain0 + c]);
+        }
+        g.n_chains = (int)gch.size() - g.chain_off;
+    }
     CK(h, cudaMemcpyAsync(h->d_chains, h->chains.data(), sizeof(Chain) * h->chains.size(), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->d_gchains, gch.data(), sizeof(Chain) * gch.size(), cudaMemcpyHostToDevice, h->st));
     return BDECON_OK;
 }
 
@@ -355,6 +385,7 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
     }
     h->o_imgs = A.take(sizeof(Image) * probs.size());
     h->o_chains = A.take(sizeof(Chain) * chh.size());
+    h->o_gchains = A.take(sizeof(Chain) * chh.size());
     h->o_err = A.take(64);
     h->o_out = A.take(64);
     h->up_bytes = up;
@@ -442,6 +473,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
     if (cudaMemsetAsync(h->arena, 0, need, h->st) != cudaSuccess) return bail(fail(h, BDECON_ERR_CUDA, "memset"));
     h->d_imgs = (Image*)(h->arena + h->o_imgs);
     h->d_chains = (Chain*)(h->arena + h->o_chains);
+    h->d_gchains = (Chain*)(h->arena + h->o_gchains);
     h->d_err = (int*)(h->arena + h->o_err);
     h->d_out = (double*)(h->arena + h->o_out);
     h->d_up = (double*)(h->arena + h->o_up);
@@ -467,6 +499,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         im.patch_off = (const int64_t*)(A + ph.o_poff);
         im.spec_len = ph.spec_len;
         im.n_ent = (int)ph.ent_kl.size();
+        im.team = problem_team(ph.L, ph.p.n_chains, ph.n_patches, ph.p.team_warps);
         im.n_tw = ph.n_tw;
         im.max_nhalf = ph.max_nhalf;
     }
@@ -533,6 +566,24 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
             const Chain& ch = h->chains[ph.chain0 + c];
             if (refresh(h, ph.chain0 + c, 1, ch.trace) != BDECON_OK) return bail(BDECON_ERR_CUDA);
         }
+    }
+    h->prob_group.assign(n, -1);
+    for (int k = 0; k < n; ++k) {
+        int gi = -1;
+        for (size_t q = 0; q < h->groups.size(); ++q)
+            if (h->groups[q].L == h->probs[k].L && h->groups[q].S == h->probs[k].S &&
+                h->groups[q].team == h->imgs[k].team)
+                gi = (int)q;
+        if (gi < 0) {
+            Group g;
+            g.L = h->probs[k].L;
+            g.S = h->probs[k].S;
+            g.team = h->imgs[k].team;
+            h->groups.push_back(g);
+            gi = (int)h->groups.size() - 1;
+        }
+        h->groups[gi].probs.push_back(k);
+        h->prob_group[k] = gi;
     }
     bdecon_status s = make_plan(h);
     if (s != BDECON_OK) return bail(s);
@@ -620,17 +671,7 @@ bdecon_status bdecon_sweep(bdecon_handle* h, int32_t n)
         int len = std::min(n, kMaxSlots);
         for (auto& ph : h->probs)
             if (ph.p.refresh_every > 0) len = std::min(len, (t0 / ph.p.refresh_every + 1) * ph.p.refresh_every - t0);
-        for (size_t ci = 0; ci < h->chains.size(); ++ci) {
-            const Chain& ch = h->chains[ci];
-            const ProbHost& ph = h->probs[ch.img];
-            CK(h, cudaMemsetAsync(ch.trace_part, 0, 8 * (size_t)len * ph.n_patches, h->st));
-            CK(h, cudaMemsetAsync(ch.prog, 0, 4 * (size_t)ph.n_patches, h->st));
-            CK(h, cudaMemsetAsync(ch.acc_step, 0, 4 * (size_t)ph.n_patches, h->st));
-        }
-        SweepArgs a;
-        a.imgs = h->d_imgs; a.chains = h->d_chains; a.n_chains = (int)h->chains.size();
-        a.t0 = t0; a.n_sweeps = len; a.err = h->d_err; a.resident = h->resident;
-        a.wait_ns = h->wait_ns; a.silent_block = h->silent_block;
+        launch_reset(h->d_imgs, h->d_chains, (int)h->chains.size(), len, h->st, &h->launches);
         cudaEvent_t ev0 = nullptr, ev1 = nullptr;
         if (h->timing) {
             if (h->ev_used + 2 > h->ev_pool.size()) {
@@ -645,13 +686,20 @@ bdecon_status bdecon_sweep(bdecon_handle* h, int32_t n)
             h->ev_used += 2;
             CK(h, cudaEventRecord(ev0, h->st));
         }
-        cudaError_t e = h->precision == BDECON_FP32 ? launch_sweep<float>(a, h->grid, h->threads, h->smem, h->st)
-                                                    : launch_sweep<double>(a, h->grid, h->threads, h->smem, h->st);
+        for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+            const Group& g = h->groups[gi];
+            SweepArgs a;
+            a.imgs = h->d_imgs; a.chains = h->d_gchains + g.chain_off; a.n_chains = g.n_chains;
+            a.t0 = t0; a.n_sweeps = len; a.err = h->d_err; a.resident = g.resident;
+            a.wait_ns = h->wait_ns; a.silent_block = gi == 0 ? h->silent_block : -1;
+            cudaError_t e = h->precision == BDECON_FP32 ? launch_sweep<float>(a, g.grid, g.threads, g.smem, h->st)
+                                                        : launch_sweep<double>(a, g.grid, g.threads, g.smem, h->st);
+            if (e != cudaSuccess)
+                return fail(h, BDECON_ERR_CUDA, "sweep launch (%d blocks x %d threads, %zu B shared): %s", g.grid,
+                            g.threads, g.smem, cudaGetErrorString(e));
+            ++h->launches;
+        }
         if (h->timing) CK(h, cudaEventRecord(ev1, h->st));
-        if (e != cudaSuccess)
-            return fail(h, BDECON_ERR_CUDA, "sweep launch (%d blocks x %d threads, %zu B shared): %s", h->grid,
-                        h->threads, h->smem, cudaGetErrorString(e));
-        ++h->launches;
         launch_trace(h->d_imgs, h->d_chains, (int)h->chains.size(), t0, len, h->st, &h->launches);
         CK(h, cudaGetLastError());
         h->sweeps += len;
@@ -834,8 +882,8 @@ bdecon_status bdecon_delta(bdecon_handle* h, int32_t p, int32_t c, int64_t m, do
     const ProbHost& ph = h->probs[p];
     if (m < 0 || m >= (int64_t)ph.Ho * ph.Wo) return fail(h, BDECON_ERR_INVALID, "pixel %lld out of range", (long long)m);
     if (!(std::isfinite(rho_new) && rho_new > 0.0)) return fail(h, BDECON_ERR_INVALID, "rho_new must be finite and > 0");
-    if (h->precision == BDECON_FP32) launch_delta<float>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, ph.L, h->st, &h->launches);
-    else launch_delta<double>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, ph.L, h->st, &h->launches);
+    if (h->precision == BDECON_FP32) launch_delta<float>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, h->imgs[p].team, h->st, &h->launches);
+    else launch_delta<double>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, h->imgs[p].team, h->st, &h->launches);
     CK(h, cudaGetLastError());
     double r[3];
     CK(h, cudaMemcpyAsync(r, h->d_out, sizeof r, cudaMemcpyDeviceToHost, h->st));
@@ -850,23 +898,24 @@ bdecon_status bdecon_set_plan(bdecon_handle* h, int32_t p, int32_t tile_i, int32
     if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
     if (p < 0 || p >= (int)h->probs.size()) return fail(h, BDECON_ERR_INVALID, "problem index %d", p);
     ProbHost& ph = h->probs[p];
-    const int old_i = ph.tpi, old_j = ph.tpj, old_w = h->warps;
-    const bool old_u = ph.user_plan, old_uw = h->user_warps;
+    Group& g = h->groups[h->prob_group[p]];
+    const int old_i = ph.tpi, old_j = ph.tpj, old_w = g.warps;
+    const bool old_u = ph.user_plan, old_uw = g.user_warps;
     if (tile_i == 0) {
         ph.user_plan = false;
-        h->user_warps = false;
+        g.user_warps = false;
     } else {
         if (tile_i < 1 || tile_j < 1 || warps < 1 || warps > 8) return fail(h, BDECON_ERR_INVALID, "bad plan");
         ph.user_plan = true;
         ph.tpi = std::min(tile_i, ph.npi);
         ph.tpj = std::min(tile_j, ph.npj);
-        h->warps = warps;
-        h->user_warps = true;
+        g.warps = warps;
+        g.user_warps = true;
     }
     bdecon_status s = check_device(h);
     if (s == BDECON_OK) s = make_plan(h);
     if (s != BDECON_OK) {
-        ph.tpi = old_i; ph.tpj = old_j; h->warps = old_w; ph.user_plan = old_u; h->user_warps = old_uw;
+        ph.tpi = old_i; ph.tpj = old_j; g.warps = old_w; ph.user_plan = old_u; g.user_warps = old_uw;
         std::string m = h->err;
         make_plan(h);
         h->err = m;
@@ -879,8 +928,9 @@ bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int3
 {
     if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
     if (p < 0 || p >= (int)h->probs.size()) return fail(h, BDECON_ERR_INVALID, "problem index %d", p);
-    if (blocks) *blocks = h->grid;
-    if (warps) *warps = h->warps;
+    const Group& g = h->groups[h->prob_group[p]];
+    if (blocks) *blocks = g.grid;
+    if (warps) *warps = g.warps;
     if (tile_i) *tile_i = h->probs[p].tpi;
     if (tile_j) *tile_j = h->probs[p].tpj;
     return BDECON_OK;
@@ -896,7 +946,7 @@ bdecon_status bdecon_launch_count(const bdecon_handle* h, int64_t* launches)
 bdecon_status bdecon_set_fault(bdecon_handle* h, int32_t silent_block, int64_t wait_ns)
 {
     if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
-    if (silent_block >= h->grid) return fail(h, BDECON_ERR_INVALID, "block %d out of range", silent_block);
+    if (silent_block >= h->groups[0].grid) return fail(h, BDECON_ERR_INVALID, "block %d out of range", silent_block);
     if (wait_ns < 1000000 || wait_ns > 60000000000ll) return fail(h, BDECON_ERR_INVALID, "wait limit out of range");
     h->silent_block = silent_block < 0 ? -1 : silent_block;
     h->wait_ns = (unsigned long long)wait_ns;

@@ -45,6 +45,7 @@ class Problem:
     refresh_every: int = 50
     truth: Optional[np.ndarray] = None
     name: str = ""
+    team_warps: int = 0          # 0 -> chosen by the library from the problem alone
 
     @property
     def H(self) -> int:

@@ -34,7 +34,7 @@ def _problem_struct(prob, **over):
     psf = np.ascontiguousarray(prob.psf, dtype=np.float64)
     keep = [img, psf]
     p = bdecon._Problem(prob.H, prob.W, img.ctypes.data, prob.L, psf.ctypes.data, None, 2.0, None, 100.0,
-                        None, 2.56, 0, 1, 0, 0.2, 0, 10, bdecon.BDECON_FP32, 64, 0)
+                        None, 2.56, 0, 1, 0, 0.2, 0, 10, bdecon.BDECON_FP32, 64, 0, 0)
     for k, v in over.items():
         setattr(p, k, v)
     return p, keep
@@ -51,6 +51,7 @@ def _problem_struct(prob, **over):
     ("H", 0, "frame size"),
     ("step", float("nan"), "step"),
     ("refresh_every", -1, "negative"),
+    ("team_warps", 9, "team_warps"),
 ])
 def test_invalid_problem_refused(field, value, msg):
     L = bdecon.load()

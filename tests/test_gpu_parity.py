@@ -287,3 +287,12 @@ def test_non_finite_expected_image_is_reported():
         s.set_state(rho, 0)
     assert ei.value.status == 6
     s.close()
+
+
+@pytest.mark.parametrize("team_warps", [1, 3])
+def test_fp64_exact_chain_with_explicit_team(team_warps):
+    # the team size fixes only the order of the per-update reductions; every
+    # team gives the oracle's chain in double precision
+    prob = synth.small_problem(H=22, W=21, L=11, sigma=1.6, seed=71, maps=True, refresh_every=4, burn_in=2)
+    prob.team_warps = team_warps
+    _compare_exact(prob, 8)
