@@ -175,8 +175,10 @@ def flops_per_update(prob, mu):
 # ---------------------------------------------------------- batched form --
 def run_batched(stream, sweeps=2, warm=1, n_images=64):
     """The batched float form: 64 uneven frames (sides 128..1024, PSF sigma
-    1..4 px, support 2 ceil(3 sigma)+1) x 4 chains in one handle; one
-    cooperative launch per PSF side and sweep segment."""
+    1..4 px, support 2 ceil(3 sigma)+1) x 4 chains in one handle.  Timed
+    first in the automatic plan (one cooperative launch per PSF side), then
+    after the library's autotuner picked the launch shapes, with every sweep
+    call replayed as one CUDA graph."""
     import torch
     from paper_2411_00991_gb300 import bdecon
     probs = synth.batch_uneven(n_images)
@@ -184,23 +186,74 @@ def run_batched(stream, sweeps=2, warm=1, n_images=64):
         q.burn_in = 0
         q.refresh_every = 50
     upd = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * q.n_chains for q in probs)
-    s = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=warm + sweeps + 4, stream=stream)
-    s.sweep(warm)
-    s.sync()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    n0 = s.launch_count()
-    e0.record()
-    s.sweep(sweeps)
-    e1.record()
-    torch.cuda.synchronize()
-    s.sync()
-    ms = e0.elapsed_time(e1)
-    groups = len({(q.L, q.n_chains * ((q.H + 2 * q.R + q.L - 1) // q.L) * ((q.W + 2 * q.R + q.L - 1) // q.L) >= 2048) for q in probs})
+    s = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=2 * (warm + sweeps) + 8, stream=stream)
+
+    def timed():
+        s.sweep(warm)
+        s.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n0 = s.launch_count()
+        e0.record()
+        s.sweep(sweeps)
+        e1.record()
+        torch.cuda.synchronize()
+        s.sync()
+        return e0.elapsed_time(e1), s.launch_count() - n0
+
+    ms_auto, _ = timed()
+    t = time.perf_counter()
+    tune = s.autotune(trial_sweeps=1)
+    tune_s = time.perf_counter() - t
+    s.set_graph(True)
+    ms, launches = timed()
+    groups = len({json.dumps(s.get_plan(p)) for p in range(len(probs))})
     out = dict(value=upd * sweeps / (ms / 1e3), unit="pixel-updates/s", images=len(probs),
                chains=sum(q.n_chains for q in probs), updates_per_sweep=upd, sweeps=sweeps,
-               ms_per_sweep=ms / sweeps, launch_groups=groups, gpu_launches=s.launch_count() - n0)
+               ms_per_sweep=ms / sweeps, gpu_launches=launches, cuda_graph=True,
+               autotune=dict(one_launch=tune["one_launch"], trial_ms_per_sweep=tune["ms_per_sweep"],
+                             seconds=tune_s),
+               distinct_plans=groups,
+               automatic_plan=dict(value=upd * sweeps / (ms_auto / 1e3), ms_per_sweep=ms_auto / sweeps))
     s.close()
     return out
+
+
+# --------------------------------------------------------------- serving --
+def run_serving(n_jobs=8, sweeps=500, rate=20.0, budget_gb=120):
+    """The serving form: deconvolution jobs (filament frames, sides
+    log-uniform in 128..2048 rounded to 32, PSF sigma U[1, 4] px, sCMOS maps,
+    one chain, float sweeps with a double refresh every 50, burn-in 250)
+    arrive as a Poisson stream of the given rate and are submitted to the
+    library's serving loop, which admits them under a device-memory budget
+    and sweeps all running jobs in shared launches.  The first n_jobs
+    arrivals of the stream are served; latency = finish - arrival."""
+    from paper_2411_00991_gb300 import bdecon
+    ta, sides, sig = synth.serving_arrivals(n_jobs, rate=rate, seed=4)
+    jobs = [synth.serving_job(int(sides[k]), float(sig[k]), seed=1000 + k) for k in range(n_jobs)]
+    upd = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * q.n_chains * sweeps for q in jobs)
+    h2d = sum(q.image.nbytes + np.asarray(q.offset).nbytes + np.asarray(q.var).nbytes + q.psf.nbytes for q in jobs)
+    d2h = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * 8 for q in jobs)
+    srv = bdecon.Server(mem_budget=int(budget_gb) << 30, max_jobs=64, segment_sweeps=25,
+                        precision=bdecon.BDECON_FP32)
+    t0 = time.perf_counter()
+    ids = []
+    for k, q in enumerate(jobs):
+        while time.perf_counter() - t0 < ta[k] - ta[0]:
+            time.sleep(0.0005)
+        ids.append(srv.submit(q, sweeps))
+    res = [srv.result(i, timeout=1800) for i in ids]
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([r[1][2] - (r[1][0]) for r in res])
+    for m, _ in res:
+        assert np.isfinite(m).all()
+    return dict(value=upd / wall, unit="pixel-updates/s", jobs=n_jobs, sweeps_per_job=sweeps,
+                arrival_rate_per_s=rate, sides=[int(x) for x in sides], psf_sigma=[round(float(x), 3) for x in sig],
+                memory_budget_gb=budget_gb, wall_s=wall, jobs_per_s=n_jobs / wall,
+                latency_p50_s=float(np.percentile(lat, 50)), latency_p99_s=float(np.percentile(lat, 99)),
+                queue_wait_p50_s=float(np.percentile([r[1][1] - r[1][0] for r in res], 50)),
+                segments=stats["segments"], h2d_bytes=int(h2d), d2h_bytes=int(d2h))
 
 
 # ---------------------------------------------------------------- our arm --
@@ -309,6 +362,9 @@ def run_ours(args):
     batched = None
     if rank == 0 and not args.no_batch:
         batched = run_batched(stream.cuda_stream)
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = run_serving(n_jobs=args.serve_jobs)
 
     if rank != 0:
         if world > 1:
@@ -358,6 +414,7 @@ def run_ours(args):
                         "peak_source": peaks["source"]},
         "fp64": fp64,
         "batched": batched,
+        "serving": serving,
         "acceptance": float(acc[-K * S:].sum() / (K * S * Ho * Wo)),
         "trace_last": float(tr[-1]),
     }
@@ -435,6 +492,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=8)
     ap.add_argument("--fp64-sweeps", type=int, default=20)
     ap.add_argument("--profile", type=int, default=0, help="ncu mode: one launch of this many sweeps")
     ap.add_argument("--profile-fp64", action="store_true")

@@ -208,15 +208,42 @@ bdecon_status bdecon_delta(bdecon_handle* h, int32_t p, int32_t c, int64_t m, do
 /* ------------------------------------------------------------- scheduling */
 
 /* Override the launch plan of problem p: tile = tile_i x tile_j patches
- * per thread block, warps per block.  Any plan gives bit-identical results
- * (each update's arithmetic and reduction order are fixed by L alone); a
- * plan whose blocks cannot all be resident is refused with
- * BDECON_ERR_INVALID.  tile_i = 0 restores the automatic plan.             */
+ * per thread block (0 for either: automatic tiles), warps per block of the
+ * problem's launch group (1..8, at least the update team's; 0: the team's
+ * own).  Any plan gives bit-identical results (each update's arithmetic and
+ * reduction order are fixed by L alone); a plan whose blocks cannot all be
+ * resident is refused with BDECON_ERR_INVALID and the previous plan kept.   */
 bdecon_status bdecon_set_plan(bdecon_handle* h, int32_t p, int32_t tile_i, int32_t tile_j,
                               int32_t warps);
 
 /* Launch plan in use: blocks of the sweep kernel, warps per block, tile
  * shape of problem p.                                                       */
+/* CUDA-graph mode (enable = 1): each bdecon_sweep call runs as one graph
+ * launch; its kernels (per segment: reset, the sweep launches, trace, double
+ * refreshes) are captured on first use for that segment sequence and
+ * replayed after (up to 8 sequences cached; a new plan or fault setting
+ * drops them).  Results are identical to plain launches.  With timing on,
+ * bdecon_sweep_kernel_time then reports whole-graph durations.  enable = 0
+ * returns to plain launches.                                               */
+bdecon_status bdecon_set_graph(bdecon_handle* h, int32_t enable);
+
+/* Launch grouping: 0 (default) = one cooperative launch per group of
+ * problems sharing PSF side, stride and update team; 1 = one launch over
+ * every problem (block size the largest team, shared memory the largest
+ * tile plan).  Resets warps set by bdecon_set_plan.  Results do not change. */
+bdecon_status bdecon_set_grouping(bdecon_handle* h, int32_t one_launch);
+
+/* Autotuner: times trial segments of trial_sweeps sweeps (1..64) for each
+ * launch shape -- per-group launches with 1x/2x/4x the team's warps, tile
+ * state resident in shared memory or streamed from global, each group tuned
+ * on its own; and the same shapes as one launch over every problem -- keeps
+ * the fastest, and restores the chains exactly (a device copy of the whole
+ * workspace is taken first: BDECON_ERR_NOMEM if it does not fit).  Tiles
+ * become automatic.  Outputs (optional): the grouping chosen and the
+ * measured device milliseconds per sweep.  Synchronous.                   */
+bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* one_launch,
+                              double* ms_per_sweep);
+
 bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int32_t* warps,
                               int32_t* tile_i, int32_t* tile_j);
 
@@ -239,6 +266,62 @@ bdecon_status bdecon_set_fault(bdecon_handle* h, int32_t silent_block, int64_t w
  * launches measured since the last call, and resets both.                  */
 bdecon_status bdecon_set_timing(bdecon_handle* h, int32_t enable);
 bdecon_status bdecon_sweep_kernel_time(bdecon_handle* h, double* ms, int64_t* launches);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A serving loop with continuous batching: a library thread admits queued
+ * jobs (one problem each) when a job slot is free and the job's device
+ * workspace fits the memory budget, sweeps all running jobs together (per segment
+ * of at most segment_sweeps sweeps, one cooperative launch per group of
+ * jobs sharing PSF side, stride and update team, or one over every job), and between segments
+ * retires finished jobs -- keeping their posterior mean for polling -- and
+ * admits new ones.  Chain state stays resident on the device while a job
+ * runs.  A job's chains use their own sweep counter, refresh schedule and
+ * random stream, so each result is bit-identical to the same job run alone.
+ * Errors of submit/poll/wait are reported through bdecon_last_error(NULL). */
+typedef struct bdecon_server bdecon_server;
+
+typedef struct {
+    size_t mem_budget;         /* device bytes for the running jobs' workspaces     */
+    int32_t max_jobs;          /* jobs running at once, >= 1                         */
+    int32_t segment_sweeps;    /* sweeps per shared segment, 1..64                  */
+    int32_t precision;         /* bdecon_precision of every job                      */
+    int32_t device;            /* CUDA device ordinal                                */
+    int32_t one_launch;        /* 1: one launch over every running job per segment   */
+} bdecon_server_config;
+
+typedef enum {
+    BDECON_JOB_QUEUED = 0,
+    BDECON_JOB_RUNNING = 1,
+    BDECON_JOB_DONE = 2,
+    BDECON_JOB_FAILED = 3
+} bdecon_job_state;
+
+/* Start the server thread on its own CUDA stream.                          */
+bdecon_status bdecon_server_start(const bdecon_server_config* cfg, bdecon_server** out);
+
+/* Queue a job of `sweeps` sweeps, more than its burn_in (inputs are copied;
+ * max_sweeps and flags of the problem are replaced).  A job whose workspace exceeds the budget is
+ * marked failed at once.                                                    */
+bdecon_status bdecon_server_submit(bdecon_server* s, const bdecon_problem* job, int32_t sweeps,
+                                   int64_t* job_id);
+
+/* State of a job; times (optional, 3 doubles, seconds on the host's steady
+ * clock) = submit, start, finish; when done and mean is non-NULL, the
+ * posterior mean over all its chains, (H+2R)*(W+2R) doubles (cap = capacity
+ * in doubles).  BDECON_ERR_STATE for a failed job.                          */
+bdecon_status bdecon_server_poll(bdecon_server* s, int64_t job_id, int32_t* state, double* times,
+                                 double* mean, size_t cap);
+
+/* Block until the job is done or failed, or timeout_s elapses.             */
+bdecon_status bdecon_server_wait(bdecon_server* s, int64_t job_id, double timeout_s, int32_t* state);
+
+bdecon_status bdecon_server_stats(bdecon_server* s, int64_t* queued, int64_t* running, int64_t* done,
+                                  size_t* mem_used, int64_t* segments);
+
+/* Stop: queued jobs fail, the running segment completes, running jobs fail,
+ * all device memory of the server and its jobs is freed.                    */
+bdecon_status bdecon_server_stop(bdecon_server* s);
 
 /* ----------------------------------------------------- allocation-free */
 

@@ -31,6 +31,11 @@ class BdeconError(RuntimeError):
         self.status = status
 
 
+class _ServerConfig(C.Structure):
+    _fields_ = [("mem_budget", C.c_size_t), ("max_jobs", C.c_int32), ("segment_sweeps", C.c_int32),
+                ("precision", C.c_int32), ("device", C.c_int32), ("one_launch", C.c_int32)]
+
+
 class _Problem(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("image", C.c_void_p),
                 ("L", C.c_int32), ("psf", C.c_void_p),
@@ -49,7 +54,11 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_accept_counts", "bdecon_accept_log", "bdecon_get_state", "bdecon_set_state",
            "bdecon_get_mu", "bdecon_log_posterior", "bdecon_delta", "bdecon_set_plan",
            "bdecon_get_plan", "bdecon_launch_count", "bdecon_set_timing", "bdecon_sweep_kernel_time",
-           "bdecon_log_posterior_static", "bdecon_set_fault"]
+           "bdecon_log_posterior_static", "bdecon_set_fault", "bdecon_server_start",
+           "bdecon_server_submit", "bdecon_server_poll", "bdecon_server_wait", "bdecon_server_stats",
+           "bdecon_server_stop", "bdecon_set_grouping", "bdecon_autotune", "bdecon_set_graph"]
+
+JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
 
 def lib_path() -> str:
@@ -92,6 +101,16 @@ def load(build_if_missing: bool = True):
         "bdecon_set_timing": [H, i32],
         "bdecon_sweep_kernel_time": [H, dp, C.POINTER(i64)],
         "bdecon_set_fault": [H, i32, i64],
+        "bdecon_set_grouping": [H, i32],
+        "bdecon_set_graph": [H, i32],
+        "bdecon_autotune": [H, i32, C.POINTER(i32), dp],
+        "bdecon_server_start": [C.POINTER(_ServerConfig), C.POINTER(vp)],
+        "bdecon_server_submit": [vp, P, i32, C.POINTER(i64)],
+        "bdecon_server_poll": [vp, i64, C.POINTER(i32), vp, vp, sz],
+        "bdecon_server_wait": [vp, i64, C.c_double, C.POINTER(i32)],
+        "bdecon_server_stats": [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(sz),
+                                C.POINTER(i64)],
+        "bdecon_server_stop": [vp],
         "bdecon_log_posterior_static": [i32, i32, vp, i32, vp, vp, C.c_double, vp, C.c_double, vp,
                                         C.c_double, i32, vp, vp, vp],
     }
@@ -120,6 +139,23 @@ def _as_map_or_scalar(v, H, W):
     return a, 0.0
 
 
+def _problem(pr, precision, max_sweeps, flags, keep) -> _Problem:
+    """Fill a bdecon_problem from a ``synth.Problem``-like object; the numpy
+    arrays it points at are appended to ``keep`` (the caller holds them until
+    the library has copied them)."""
+    img = np.ascontiguousarray(np.asarray(pr.image, dtype=np.float32))
+    psf = np.ascontiguousarray(np.asarray(pr.psf, dtype=np.float64))
+    H, W = img.shape
+    g, gs = _as_map_or_scalar(pr.gain, H, W)
+    o, os_ = _as_map_or_scalar(pr.offset, H, W)
+    v, vs = _as_map_or_scalar(pr.var, H, W)
+    keep += [img, psf, g, o, v]
+    return _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
+                    int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
+                    int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
+                    int(flags), int(getattr(pr, "team_warps", 0)))
+
+
 def log_posterior_static(H, W, image_ptr, L, psf_ptr, gain, offset, var, stride, rho_ptr, out_ptr,
                          stream=None):
     """Allocation-free log posterior (bdecon_log_posterior_static): every
@@ -141,7 +177,7 @@ def log_posterior_static(H, W, image_ptr, L, psf_ptr, gain, offset, var, stride,
                                        o, os_, v, vs, int(stride), C.c_void_p(rho_ptr), C.c_void_p(out_ptr),
                                        C.c_void_p(stream) if stream else None)
     if s != 0:
-        raise BdeconError(s, L_.bdecon_last_error(None).decode())
+        raise BdeconError(s, L_.bdecon_last_error(None).decode(errors="replace"))
 
 
 class Sampler:
@@ -158,17 +194,7 @@ class Sampler:
         self._keep = []
         arr = (_Problem * len(problems))()
         for k, pr in enumerate(problems):
-            img = np.ascontiguousarray(np.asarray(pr.image, dtype=np.float32))
-            psf = np.ascontiguousarray(np.asarray(pr.psf, dtype=np.float64))
-            H, W = img.shape
-            g, gs = _as_map_or_scalar(pr.gain, H, W)
-            o, os_ = _as_map_or_scalar(pr.offset, H, W)
-            v, vs = _as_map_or_scalar(pr.var, H, W)
-            self._keep += [img, psf, g, o, v]
-            arr[k] = _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
-                              int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
-                              int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
-                              int(flags), int(getattr(pr, "team_warps", 0)))
+            arr[k] = _problem(pr, precision, max_sweeps, flags, self._keep)
         self._arr = arr
         self.precision = precision
         h = C.c_void_p()
@@ -179,7 +205,7 @@ class Sampler:
         else:
             s = self.L.bdecon_batch_create(arr, len(problems), st, C.byref(h))
         if s != 0:
-            raise BdeconError(s, self.L.bdecon_last_error(None).decode())
+            raise BdeconError(s, self.L.bdecon_last_error(None).decode(errors="replace"))
         self.h = h
         self._keep = []   # inputs were copied by the library
 
@@ -191,27 +217,17 @@ class Sampler:
         keep = []
         arr = (_Problem * len(problems))()
         for k, pr in enumerate(problems):
-            img = np.ascontiguousarray(np.asarray(pr.image, dtype=np.float32))
-            psf = np.ascontiguousarray(np.asarray(pr.psf, dtype=np.float64))
-            H, W = img.shape
-            g, gs = _as_map_or_scalar(pr.gain, H, W)
-            o, os_ = _as_map_or_scalar(pr.offset, H, W)
-            v, vs = _as_map_or_scalar(pr.var, H, W)
-            keep += [img, psf, g, o, v]
-            arr[k] = _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
-                              int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
-                              int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
-                              int(flags), int(getattr(pr, "team_warps", 0)))
+            arr[k] = _problem(pr, precision, max_sweeps, flags, keep)
         n = C.c_size_t()
         s = L.bdecon_workspace_size(arr, len(problems), C.byref(n))
         if s != 0:
-            raise BdeconError(s, L.bdecon_last_error(None).decode())
+            raise BdeconError(s, L.bdecon_last_error(None).decode(errors="replace"))
         return int(n.value)
 
     # ----------------------------------------------------------- plumbing --
     def _ck(self, s):
         if s != 0:
-            raise BdeconError(s, self.L.bdecon_last_error(self.h).decode())
+            raise BdeconError(s, self.L.bdecon_last_error(self.h).decode(errors="replace"))
 
     def close(self):
         if getattr(self, "h", None):
@@ -302,6 +318,19 @@ class Sampler:
     def set_plan(self, tile_i: int, tile_j: int, warps: int, p: int = 0):
         self._ck(self.L.bdecon_set_plan(self.h, p, int(tile_i), int(tile_j), int(warps)))
 
+    def set_graph(self, enable: bool = True):
+        """Run each sweep() call as one CUDA-graph launch (captured once per segment sequence)."""
+        self._ck(self.L.bdecon_set_graph(self.h, int(bool(enable))))
+
+    def set_grouping(self, one_launch: bool):
+        self._ck(self.L.bdecon_set_grouping(self.h, int(bool(one_launch))))
+
+    def autotune(self, trial_sweeps: int = 2):
+        """Time the candidate launch shapes, keep the fastest; chains unchanged."""
+        one, ms = C.c_int32(), C.c_double()
+        self._ck(self.L.bdecon_autotune(self.h, int(trial_sweeps), C.byref(one), C.byref(ms)))
+        return dict(one_launch=bool(one.value), ms_per_sweep=ms.value)
+
     def get_plan(self, p: int = 0):
         b, w, ti, tj = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         self._ck(self.L.bdecon_get_plan(self.h, p, C.byref(b), C.byref(w), C.byref(ti), C.byref(tj)))
@@ -323,3 +352,73 @@ class Sampler:
         n = C.c_int64()
         self._ck(self.L.bdecon_launch_count(self.h, C.byref(n)))
         return int(n.value)
+
+
+class Server:
+    """The library's serving loop (bdecon_server_*): jobs are queued, admitted
+    by device memory and run together in shared launches by a library
+    thread; ``result`` blocks until a job is done and returns its posterior
+    mean with its (submit, start, finish) host times."""
+
+    def __init__(self, mem_budget: int, max_jobs: int = 64, segment_sweeps: int = 16,
+                 precision: int = BDECON_FP32, device: int = 0, one_launch: bool = False):
+        self.L = load()
+        cfg = _ServerConfig(int(mem_budget), int(max_jobs), int(segment_sweeps), int(precision), int(device),
+                            int(bool(one_launch)))
+        self.precision = precision
+        s = C.c_void_p()
+        self._ck(self.L.bdecon_server_start(C.byref(cfg), C.byref(s)))
+        self.s = s
+        self._shape = {}
+
+    def _ck(self, st):
+        if st != 0:
+            raise BdeconError(st, self.L.bdecon_last_error(None).decode(errors="replace"))
+
+    def submit(self, problem, sweeps: int) -> int:
+        keep = []
+        p = _problem(problem, self.precision, sweeps, 0, keep)
+        jid = C.c_int64()
+        self._ck(self.L.bdecon_server_submit(self.s, C.byref(p), int(sweeps), C.byref(jid)))
+        H, W = np.asarray(problem.image).shape
+        R = np.asarray(problem.psf).shape[0] // 2
+        self._shape[jid.value] = (H + 2 * R, W + 2 * R)
+        return int(jid.value)
+
+    def poll(self, job: int):
+        """(state, (t_submit, t_start, t_done)) of a job."""
+        st = C.c_int32()
+        t = np.zeros(3)
+        r = self.L.bdecon_server_poll(self.s, int(job), C.byref(st), _p(t), None, 0)
+        if r != 0 and st.value != JOB_FAILED:
+            self._ck(r)
+        return int(st.value), tuple(t)
+
+    def result(self, job: int, timeout: float = 600.0):
+        """Block until the job ends; (posterior mean, (t_submit, t_start, t_done))."""
+        st = C.c_int32()
+        self._ck(self.L.bdecon_server_wait(self.s, int(job), float(timeout), C.byref(st)))
+        if st.value not in (JOB_DONE, JOB_FAILED):
+            raise TimeoutError(f"job {job} not finished after {timeout} s")
+        out = np.empty(self._shape[job])
+        t = np.zeros(3)
+        self._ck(self.L.bdecon_server_poll(self.s, int(job), C.byref(st), _p(t), _p(out), out.size))
+        return out, tuple(t)
+
+    def stats(self):
+        q, r, d, seg = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        m = C.c_size_t()
+        self._ck(self.L.bdecon_server_stats(self.s, C.byref(q), C.byref(r), C.byref(d), C.byref(m),
+                                            C.byref(seg)))
+        return dict(queued=q.value, running=r.value, done=d.value, mem_used=m.value, segments=seg.value)
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.L.bdecon_server_stop(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

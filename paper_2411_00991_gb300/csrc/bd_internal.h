@@ -73,13 +73,13 @@ struct Chain {
     double* trace;                   // [sweep 0..max_sweeps]
     int tpi, tpj, nti, ntj;          // tile shape (patches) and tile grid
     int cta_base;                    // first block of this chain in the sweep grid
+    int* tdev;                       // sweeps this chain has completed (device counter, advanced by k_trace)
 };
 
 struct SweepArgs {
     const Image* imgs;
     const Chain* chains;
     int n_chains;
-    int t0;                          // sweeps completed before this launch
     int n_sweeps;                    // sweeps in this launch
     int* err;
     int resident;                    // 1: tile state (data, spectra, rho) held in shared memory
@@ -149,8 +149,10 @@ template <typename T>
 void launch_init_rho(const Image& im, const Chain& ch, const double* b0, cudaStream_t st,
                      int64_t* launches);
 template <typename T>
+// out_logpost receives the log posterior at out_logpost[*out_index] (index 0
+// when out_index is null)
 void launch_refresh(const Image& im, const Chain& ch, double* scratch, int write_state,
-                    double* out_logpost, int* err, cudaStream_t st, int64_t* launches);
+                    double* out_logpost, const int* out_index, int* err, cudaStream_t st, int64_t* launches);
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 template <typename T>
@@ -158,7 +160,7 @@ int sweep_blocks_per_sm(int threads, size_t smem);
 // zero every chain's progress words, last-accept words and trace partials
 void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_slots, cudaStream_t st,
                   int64_t* launches);
-void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int t0, int n_sweeps,
+void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_sweeps,
                   cudaStream_t st, int64_t* launches);
 template <typename T>
 void launch_delta(const Image* d_im, const Chain* d_ch, int64_t m, double rho_new, double* out3, int team,
@@ -168,6 +170,8 @@ void launch_convert(const void* src, double* dst, int64_t n, int rows, int cols,
                     cudaStream_t st, int64_t* launches);
 template <typename T>
 void launch_set_rho(const double* src, void* dst, int64_t n, cudaStream_t st, int64_t* launches);
+// sets every chain's sweep counter to value
+void launch_set_counters(const Chain* d_chains, int n_chains, int value, cudaStream_t st, int64_t* launches);
 // sets the thread-local message that bdecon_last_error(NULL) returns
 void set_host_error(const char* msg);
 void launch_mean(const double* sum, int n_chains_img, int64_t chain_stride_elems, int Ho, int Wo,

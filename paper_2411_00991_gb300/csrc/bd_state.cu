@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kRedThreads) k_refresh_spec(Image im, Chain ch
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_refresh_total(const double* part_ll, int n_ll, const double* part_lp,
-                                                              int n_lp, double* out)
+                                                              int n_lp, double* out, const int* out_index)
 {
     __shared__ double sh[kRedThreads];
     double a = 0.0, b = 0.0;
@@ -292,23 +292,25 @@ __global__ void __launch_bounds__(kRedThreads) k_refresh_total(const double* par
     for (int k = threadIdx.x; k < n_lp; k += kRedThreads) b += part_lp[k];
     const double ta = block_sum(a, sh);
     const double tb = block_sum(b, sh);
-    if (threadIdx.x == 0) out[0] = ta + tb;
+    if (threadIdx.x == 0) out[out_index ? *out_index : 0] = ta + tb;
 }
 
 template <typename T>
 void launch_refresh(const Image& im, const Chain& ch, double* scratch, int write_state, double* out_logpost,
-                    int* err, cudaStream_t st, int64_t* launches)
+                    const int* out_index, int* err, cudaStream_t st, int64_t* launches)
 {
     const int nblk = (im.H * im.W + kRedThreads - 1) / kRedThreads;
     double* part_ll = scratch;
     double* part_lp = scratch + nblk;
     k_refresh_mu<T><<<nblk, kRedThreads, 0, st>>>(im, ch, part_ll, write_state, err);
     k_refresh_spec<T><<<im.n_patches, kRedThreads, 0, st>>>(im, ch, part_lp, write_state);
-    k_refresh_total<<<1, kRedThreads, 0, st>>>(part_ll, nblk, part_lp, im.n_patches, out_logpost);
+    k_refresh_total<<<1, kRedThreads, 0, st>>>(part_ll, nblk, part_lp, im.n_patches, out_logpost, out_index);
     *launches += 3;
 }
-template void launch_refresh<float>(const Image&, const Chain&, double*, int, double*, int*, cudaStream_t, int64_t*);
-template void launch_refresh<double>(const Image&, const Chain&, double*, int, double*, int*, cudaStream_t, int64_t*);
+template void launch_refresh<float>(const Image&, const Chain&, double*, int, double*, const int*, int*, cudaStream_t,
+                                    int64_t*);
+template void launch_refresh<double>(const Image&, const Chain&, double*, int, double*, const int*, int*, cudaStream_t,
+                                     int64_t*);
 
 // ------------------------------------------------------------ reset -----
 __global__ void k_reset(const Image* imgs, const Chain* chains, int n_slots)
@@ -331,12 +333,14 @@ void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int 
 
 // ------------------------------------------------------------ trace -----
 // trace[t0 + s + 1] = trace[t0] + sum_{s' <= s} sum_p part[s'][p]: the double
-// running sum of accepted dL + dP, per chain (one block per chain).
-__global__ void __launch_bounds__(kRedThreads) k_trace(const Image* imgs, const Chain* chains, int t0, int n)
+// running sum of accepted dL + dP, per chain (one block per chain); t0 is the
+// chain's sweep counter, which this kernel then advances by n.
+__global__ void __launch_bounds__(kRedThreads) k_trace(const Image* imgs, const Chain* chains, int n)
 {
     __shared__ double sh[kRedThreads];
     const Chain& ch = chains[blockIdx.x];
     const int np = imgs[ch.img].n_patches;
+    const int t0 = *ch.tdev;
     double cum = ch.trace[t0];
     for (int s = 0; s < n; ++s) {
         double a = 0.0;
@@ -344,12 +348,26 @@ __global__ void __launch_bounds__(kRedThreads) k_trace(const Image* imgs, const 
         cum += block_sum(a, sh);
         if (threadIdx.x == 0) ch.trace[t0 + s + 1] = cum;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) *ch.tdev = t0 + n;
 }
 
-void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int t0, int n_sweeps, cudaStream_t st,
+void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_sweeps, cudaStream_t st,
                   int64_t* launches)
 {
-    k_trace<<<n_chains, kRedThreads, 0, st>>>(d_imgs, d_chains, t0, n_sweeps);
+    k_trace<<<n_chains, kRedThreads, 0, st>>>(d_imgs, d_chains, n_sweeps);
+    ++*launches;
+}
+
+__global__ void k_set_counters(const Chain* chains, int n, int value)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) *chains[k].tdev = value;
+}
+
+void launch_set_counters(const Chain* d_chains, int n_chains, int value, cudaStream_t st, int64_t* launches)
+{
+    k_set_counters<<<(n_chains + 127) / 128, 128, 0, st>>>(d_chains, n_chains, value);
     ++*launches;
 }
 

@@ -27,6 +27,9 @@
 // mu, shared with the neighbouring tiles, is read from global memory (L2).
 #include <type_traits>
 
+#include <atomic>
+#include <mutex>
+
 #include "bd_device.cuh"
 
 namespace bd {
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     __syncthreads();
     const Chain& ch = a.chains[s_ci];
     const Image& im = a.imgs[ch.img];
+    const int t0 = *ch.tdev;          // sweeps completed before this launch (advanced after it by k_trace)
     const int tl = (int)blockIdx.x - ch.cta_base;
     const int ti = tl / ch.ntj, tj = tl - (tl / ch.ntj) * ch.ntj;
     const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W, S2 = S * S, LL = L * L;
@@ -271,7 +275,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         if (sh.ph > 0 && sh.pw > 0) {
             const int m = (pi * S) * im.Wo + pj * S;
             T z, lu, rn, dl;
-            proposal<T>(im, ch, m, a.t0 + 1, RES ? rho_s[(size_t)g * S2] : rho_g[m], z, lu, rn, dl);
+            proposal<T>(im, ch, m, t0 + 1, RES ? rho_s[(size_t)g * S2] : rho_g[m], z, lu, rn, dl);
             if (lane == 0) {
                 s_prop[0][g][0] = z; s_prop[0][g][1] = lu; s_prop[0][g][2] = rn; s_prop[0][g][3] = dl;
             }
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
 
     for (int s = 0; s < nsteps; ++s) {
         const int slot = s / S2, c = s - slot * S2;
-        const int t = a.t0 + 1 + slot;
+        const int t = t0 + 1 + slot;
         const int u = c / S, v = c - (c / S) * S;
         for (int r = 0; r < rounds; ++r) {
             const int q = r * n_sub + g;
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 if (u1 < sh1.ph && v1 < sh1.pw) {
                     const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
                     T z1, lu1, rn1, dl1;
-                    proposal<T>(im, ch, m1, a.t0 + 1 + s1 / S2, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1],
+                    proposal<T>(im, ch, m1, t0 + 1 + s1 / S2, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1],
                                 z1, lu1, rn1, dl1);
                     if (lane == 0) {
                         s_prop[s1 & 1][g][0] = z1; s_prop[s1 & 1][g][1] = lu1;
@@ -484,15 +488,43 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     }
 }
 
+// Raise the kernel's dynamic shared-memory limit to at least smem (the limit
+// only grows, so launches with smaller plans stay valid).
+template <typename T, bool RES>
+cudaError_t ensure_smem_limit(size_t smem)
+{
+    static std::atomic<size_t> limit{0};
+    static std::mutex mu;
+    if (limit.load() >= smem) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(mu);
+    if (limit.load() >= smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_sweep<T, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) limit.store(smem);
+    return e;
+}
+
+// Cooperative launch (all blocks co-resident, which the neighbour waits
+// rely on), through the launch-attribute form so that it can be captured in
+// a CUDA graph.
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st)
 {
     SweepArgs args = a;
     void* kargs[] = {&args};
     const void* fn = a.resident ? (const void*)k_sweep<T, true> : (const void*)k_sweep<T, false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = a.resident ? ensure_smem_limit<T, true>(smem) : ensure_smem_limit<T, false>(smem);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), kargs, smem, st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, kargs);
 }
 
 template <typename T>
@@ -501,8 +533,12 @@ int sweep_blocks_per_sm(int threads, size_t smem)
     int n = 0, n2 = 0;
     const void* fn = (const void*)k_sweep<T, true>;
     const void* fn2 = (const void*)k_sweep<T, false>;
-    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    if (cudaFuncSetAttribute(fn2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    (void)fn;
+    (void)fn2;
+    if (ensure_smem_limit<T, true>(smem) != cudaSuccess || ensure_smem_limit<T, false>(smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, true>, threads, smem) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_sweep<T, false>, threads, smem) != cudaSuccess) return 0;
     return n < n2 ? n : n2;

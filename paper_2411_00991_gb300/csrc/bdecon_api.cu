@@ -2,7 +2,13 @@
 // argument validation, the device arena, the launch plan of the persistent
 // sweep kernel, and the sweep / refresh / trace schedule.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -53,11 +59,12 @@ struct Group {
     int grid = 0;
     size_t smem = 0;
     int resident = 1;
+    bool streamed = false;             // plan with tile state in global memory even if it fits in shared
     int chain_off = 0, n_chains = 0;   // slice of the group-ordered chain table
 };
 
 struct ChainHost {
-    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace;
+    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace, o_tdev;
 };
 
 }  // namespace
@@ -71,7 +78,9 @@ struct bdecon_handle {
     int max_sweeps = 4096;
     int64_t sweeps = 0;
     std::vector<Group> groups;
+    bool one_launch = false;            // all problems in one launch instead of one per (L, S, team)
     std::vector<int> prob_group;        // problem -> group
+    std::vector<Chain> gch;             // host copy of the group-ordered chain table
     size_t o_gchains = 0;
     Chain* d_gchains = nullptr;          // chain descriptors in group order
     bool failed = false;
@@ -93,6 +102,16 @@ struct bdecon_handle {
     unsigned long long wait_ns = 4000000000ull;
     std::vector<cudaEvent_t> ev_pool;    // pairs (start, stop), reused
     size_t ev_used = 0;
+    // CUDA-graph mode: the kernel sequence of one bdecon_sweep call, keyed by
+    // its segment lengths and refreshes, captured once and replayed
+    bool use_graph = false;
+    struct GraphEntry {
+        std::vector<int> sig;
+        cudaGraphExec_t exec = nullptr;
+        int64_t launches = 0;
+    };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap_st = nullptr;
     std::string err;
 };
 
@@ -227,11 +246,6 @@ void describe(ProbHost& ph)
     ph.spec_len = off;
 }
 
-int blocks_of(const ProbHost& ph)
-{
-    return ph.p.n_chains * ((ph.npi + ph.tpi - 1) / ph.tpi) * ((ph.npj + ph.tpj - 1) / ph.tpj);
-}
-
 int occupancy(int prec, int threads, size_t smem)
 {
     return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem) : sweep_blocks_per_sm<double>(threads, smem);
@@ -239,55 +253,73 @@ int occupancy(int prec, int threads, size_t smem)
 
 constexpr size_t kMaxSmem = 227 * 1024;
 
-size_t plan_smem(const bdecon_handle* h, const Group& g, int resident)
+// One problem's entry in a launch plan: the problem, its update team, its
+// tile shape, and its chains' descriptors in the launch's chain table.
+struct PlanItem {
+    const ProbHost* ph = nullptr;
+    int team = 32;
+    int tpi = 1, tpj = 1;
+    bool user = false;
+    std::vector<Chain*> chains;
+};
+
+int item_blocks(const PlanItem& it)
 {
-    const int ts = h->precision == BDECON_FP32 ? 4 : 8;
+    return (int)it.chains.size() * ((it.ph->npi + it.tpi - 1) / it.tpi) * ((it.ph->npj + it.tpj - 1) / it.tpj);
+}
+
+size_t items_smem(const std::vector<PlanItem*>& items, int resident, int ts)
+{
     size_t mx = 0;
-    for (int k : g.probs) {
-        const ProbHost& ph = h->probs[k];
-        const SmemPlan sp = smem_plan(ph.L, ph.S, ph.n_tw, (int)ph.ent_kl.size(), ph.max_nhalf, ph.tpi, ph.tpj,
+    for (const PlanItem* it : items) {
+        const ProbHost& ph = *it->ph;
+        const SmemPlan sp = smem_plan(ph.L, ph.S, ph.n_tw, (int)ph.ent_kl.size(), ph.max_nhalf, it->tpi, it->tpj,
                                       resident, ts);
         mx = std::max(mx, sp.total);
     }
     return mx;
 }
 
-// Grow the tile of the group's problem with the most blocks; false if none can grow.
-bool grow_worst(bdecon_handle* h, const Group& g)
+// Grow the tile of the problem with the most blocks; false if none can grow.
+bool grow_items(std::vector<PlanItem*>& items)
 {
-    int worst = -1, wb = -1;
-    for (int k : g.probs) {
-        const ProbHost& ph = h->probs[k];
-        const int b = blocks_of(ph);
-        if (!ph.user_plan && !(ph.tpi >= ph.npi && ph.tpj >= ph.npj) && b > wb) { wb = b; worst = k; }
+    PlanItem* worst = nullptr;
+    int wb = -1;
+    for (PlanItem* it : items) {
+        const int b = item_blocks(*it);
+        if (!it->user && !(it->tpi >= it->ph->npi && it->tpj >= it->ph->npj) && b > wb) {
+            wb = b;
+            worst = it;
+        }
     }
-    if (worst < 0) return false;
-    ProbHost& ph = h->probs[worst];
-    if ((ph.tpj <= ph.tpi && ph.tpj < ph.npj) || ph.tpi >= ph.npi) ++ph.tpj; else ++ph.tpi;
+    if (!worst) return false;
+    if ((worst->tpj <= worst->tpi && worst->tpj < worst->ph->npj) || worst->tpi >= worst->ph->npi) ++worst->tpj;
+    else ++worst->tpi;
     return true;
 }
 
-// Launch plan of one group: block = the update team of its PSF side (or the
-// user's warps); tiles grow from one patch until every block of every chain
-// of the group is co-resident.  Resident plans (tile state in shared memory)
-// are preferred; if none fits, tile state is streamed from global memory.
-bdecon_status plan_group(bdecon_handle* h, Group& g)
+// Launch plan of one group: block = the group's update team (or the user's
+// warps); tiles grow from one patch until every block of every chain of the
+// group is co-resident.  Resident plans (tile state in shared memory) are
+// preferred; if none fits, tile state is streamed from global memory.
+bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g, std::string& err)
 {
     int team = 32;
-    for (int k : g.probs) team = std::max(team, h->imgs[k].team);
+    for (const PlanItem* it : items) team = std::max(team, it->team);
     g.threads = g.user_warps ? std::max(32 * g.warps, team) : team;
     g.warps = g.threads / 32;
+    const int ts = precision == BDECON_FP32 ? 4 : 8;
     bool done = false;
-    for (int resident = 1; resident >= 0 && !done; --resident) {
-        for (int k : g.probs)
-            if (!h->probs[k].user_plan) h->probs[k].tpi = h->probs[k].tpj = 1;
+    for (int resident = g.streamed ? 0 : 1; resident >= 0 && !done; --resident) {
+        for (PlanItem* it : items)
+            if (!it->user) it->tpi = it->tpj = 1;
         for (;;) {
-            const size_t smem = plan_smem(h, g, resident);
+            const size_t smem = items_smem(items, resident, ts);
             int tot = 0;
-            for (int k : g.probs) tot += blocks_of(h->probs[k]);
+            for (const PlanItem* it : items) tot += item_blocks(*it);
             if (smem <= kMaxSmem) {
-                const int bps = occupancy(h->precision, g.threads, smem);
-                if (bps > 0 && tot <= bps * h->sms) {
+                const int bps = occupancy(precision, g.threads, smem);
+                if (bps > 0 && tot <= bps * sms) {
                     g.smem = smem;
                     g.resident = resident;
                     done = true;
@@ -296,46 +328,101 @@ bdecon_status plan_group(bdecon_handle* h, Group& g)
             } else if (resident) {
                 break;   // tiles only grow: resident state will not fit
             }
-            if (!grow_worst(h, g)) break;
+            if (!grow_items(items)) break;
         }
     }
     if (!done) {
         int tot = 0;
-        for (int k : g.probs) tot += blocks_of(h->probs[k]);
-        return fail(h, BDECON_ERR_INVALID, "no launch plan: %d blocks of %d threads cannot all be co-resident", tot,
-                    g.threads);
+        for (const PlanItem* it : items) tot += item_blocks(*it);
+        char buf[160];
+        snprintf(buf, sizeof buf, "no launch plan: %d blocks of %d threads cannot all be co-resident", tot, g.threads);
+        err = buf;
+        return false;
     }
     int base = 0;
-    for (int k : g.probs) {
-        ProbHost& ph = h->probs[k];
-        const int nti = (ph.npi + ph.tpi - 1) / ph.tpi, ntj = (ph.npj + ph.tpj - 1) / ph.tpj;
-        for (int c = 0; c < ph.p.n_chains; ++c) {
-            Chain& ch = h->chains[ph.chain0 + c];
-            ch.tpi = ph.tpi; ch.tpj = ph.tpj; ch.nti = nti; ch.ntj = ntj;
-            ch.cta_base = base;
+    for (PlanItem* it : items) {
+        const int nti = (it->ph->npi + it->tpi - 1) / it->tpi, ntj = (it->ph->npj + it->tpj - 1) / it->tpj;
+        for (Chain* ch : it->chains) {
+            ch->tpi = it->tpi; ch->tpj = it->tpj; ch->nti = nti; ch->ntj = ntj;
+            ch->cta_base = base;
             base += nti * ntj;
         }
     }
     g.grid = base;
+    return true;
+}
+
+void drop_graphs(bdecon_handle* h)
+{
+    for (auto& g : h->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+// The handle's own plan: one group per (L, S, team) of its problems.
+bdecon_status make_plan(bdecon_handle* h)
+{
+    drop_graphs(h);   // captured launches carry the old grid and tables
+    for (auto& g : h->groups) {
+        std::vector<PlanItem> items(g.probs.size());
+        std::vector<PlanItem*> ptrs;
+        for (size_t k = 0; k < g.probs.size(); ++k) {
+            ProbHost& ph = h->probs[g.probs[k]];
+            PlanItem& it = items[k];
+            it.ph = &ph;
+            it.team = h->imgs[g.probs[k]].team;
+            it.tpi = ph.tpi;
+            it.tpj = ph.tpj;
+            it.user = ph.user_plan;
+            for (int c = 0; c < ph.p.n_chains; ++c) it.chains.push_back(&h->chains[ph.chain0 + c]);
+            ptrs.push_back(&it);
+        }
+        std::string err;
+        if (!plan_items(h->precision, h->sms, ptrs, g, err)) return fail(h, BDECON_ERR_INVALID, "%s", err.c_str());
+        for (size_t k = 0; k < g.probs.size(); ++k) {
+            h->probs[g.probs[k]].tpi = items[k].tpi;
+            h->probs[g.probs[k]].tpj = items[k].tpj;
+        }
+    }
+    h->gch.clear();
+    for (auto& g : h->groups) {
+        g.chain_off = (int)h->gch.size();
+        for (int k : g.probs) {
+            const ProbHost& ph = h->probs[k];
+            for (int c = 0; c < ph.p.n_chains; ++c) h->gch.push_back(h->chains[ph.chain0 + c]);
+        }
+        g.n_chains = (int)h->gch.size() - g.chain_off;
+    }
+    CK(h, cudaMemcpyAsync(h->d_chains, h->chains.data(), sizeof(Chain) * h->chains.size(), cudaMemcpyHostToDevice, h->st));
+    CK(h, cudaMemcpyAsync(h->d_gchains, h->gch.data(), sizeof(Chain) * h->gch.size(), cudaMemcpyHostToDevice, h->st));
     return BDECON_OK;
 }
 
-bdecon_status make_plan(bdecon_handle* h)
+// Launch groups: one per (L, S, team), or a single group when one_launch is
+// set (the kernel reads each block's problem from its chain; the block size
+// is then the largest team and the shared memory the largest tile plan).
+void form_groups(bdecon_handle* h)
 {
-    std::vector<Chain> gch;
-    for (auto& g : h->groups) {
-        bdecon_status s = plan_group(h, g);
-        if (s != BDECON_OK) return s;
-        g.chain_off = (int)gch.size();
-        for (int k : g.probs) {
-            const ProbHost& ph = h->probs[k];
-            for (int c = 0; c < ph.p.n_chains; ++c) gch.push_back(h->chains[ph.chain0 + c]);
+    const int n = (int)h->probs.size();
+    h->groups.clear();
+    h->prob_group.assign(n, -1);
+    for (int k = 0; k < n; ++k) {
+        int gi = -1;
+        for (size_t q = 0; q < h->groups.size() && gi < 0; ++q)
+            if (h->one_launch || (h->groups[q].L == h->probs[k].L && h->groups[q].S == h->probs[k].S &&
+                                  h->groups[q].team == h->imgs[k].team))
+                gi = (int)q;
+        if (gi < 0) {
+            Group g;
+            g.L = h->probs[k].L;
+            g.S = h->probs[k].S;
+            g.team = h->imgs[k].team;
+            h->groups.push_back(g);
+            gi = (int)h->groups.size() - 1;
         }
-        g.n_chains = (int)gch.size() - g.chain_off;
+        h->groups[gi].probs.push_back(k);
+        h->prob_group[k] = gi;
     }
-    CK(h, cudaMemcpyAsync(h->d_chains, h->chains.data(), sizeof(Chain) * h->chains.size(), cudaMemcpyHostToDevice, h->st));
-    CK(h, cudaMemcpyAsync(h->d_gchains, gch.data(), sizeof(Chain) * gch.size(), cudaMemcpyHostToDevice, h->st));
-    return BDECON_OK;
 }
 
 size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainHost>& chh, int prec, int max_sweeps)
@@ -380,6 +467,7 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
             x.o_prog = A.take(4 * (size_t)ph.n_patches);
             x.o_astep = A.take(4 * (size_t)ph.n_patches);
             x.o_trace = A.take(8 * ((size_t)max_sweeps + 1));
+            x.o_tdev = A.take(4);
             chh.push_back(x);
         }
     }
@@ -394,19 +482,23 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
     return align_up(A.off, 256);
 }
 
+// Double refresh of chain ci (mu, spectra, cumulant cache when write is set)
+// and its log posterior into out[*idx] (out[0] when idx is null).
 template <typename T>
-bdecon_status refresh_chain(bdecon_handle* h, int ci, int write, double* out)
+bdecon_status refresh_chain(bdecon_handle* h, int ci, int write, double* out, const int* idx)
 {
     const Chain& ch = h->chains[ci];
     const ProbHost& ph = h->probs[ch.img];
-    launch_refresh<T>(h->imgs[ch.img], ch, (double*)(h->arena + ph.o_scr), write, out, h->d_err, h->st, &h->launches);
+    launch_refresh<T>(h->imgs[ch.img], ch, (double*)(h->arena + ph.o_scr), write, out, idx, h->d_err, h->st,
+                      &h->launches);
     CK(h, cudaGetLastError());
     return BDECON_OK;
 }
 
-bdecon_status refresh(bdecon_handle* h, int ci, int write, double* out)
+bdecon_status refresh(bdecon_handle* h, int ci, int write, double* out, const int* idx = nullptr)
 {
-    return h->precision == BDECON_FP32 ? refresh_chain<float>(h, ci, write, out) : refresh_chain<double>(h, ci, write, out);
+    return h->precision == BDECON_FP32 ? refresh_chain<float>(h, ci, write, out, idx)
+                                       : refresh_chain<double>(h, ci, write, out, idx);
 }
 
 bdecon_status check_device(bdecon_handle* h)
@@ -524,6 +616,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
             ch.prog = (int*)(A + x.o_prog);
             ch.acc_step = (int*)(A + x.o_astep);
             ch.trace = (double*)(A + x.o_trace);
+            ch.tdev = (int*)(A + x.o_tdev);
         }
     }
     if (cudaMemcpyAsync(h->d_imgs, h->imgs.data(), sizeof(Image) * n, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
@@ -567,29 +660,216 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
             if (refresh(h, ph.chain0 + c, 1, ch.trace) != BDECON_OK) return bail(BDECON_ERR_CUDA);
         }
     }
-    h->prob_group.assign(n, -1);
-    for (int k = 0; k < n; ++k) {
-        int gi = -1;
-        for (size_t q = 0; q < h->groups.size(); ++q)
-            if (h->groups[q].L == h->probs[k].L && h->groups[q].S == h->probs[k].S &&
-                h->groups[q].team == h->imgs[k].team)
-                gi = (int)q;
-        if (gi < 0) {
-            Group g;
-            g.L = h->probs[k].L;
-            g.S = h->probs[k].S;
-            g.team = h->imgs[k].team;
-            h->groups.push_back(g);
-            gi = (int)h->groups.size() - 1;
-        }
-        h->groups[gi].probs.push_back(k);
-        h->prob_group[k] = gi;
-    }
+    form_groups(h);
     bdecon_status s = make_plan(h);
     if (s != BDECON_OK) return bail(s);
     s = check_device(h);
     if (s != BDECON_OK) return bail(s);
     *out = h;
+    return BDECON_OK;
+}
+
+
+// A launch over one or more handles (all of one precision on one device):
+// the groups, the host copy of the launch's chain table (group order), the
+// owning handle of each chain, and the device tables the kernel reads.
+struct LaunchSet {
+    std::vector<bdecon_handle*> hs;
+    std::vector<Group> groups;
+    std::vector<Chain> gch;
+    std::vector<int> owner;
+    const Image* d_imgs = nullptr;
+    Chain* d_gch = nullptr;
+};
+
+void own_launch_set(bdecon_handle* h, LaunchSet& ls)
+{
+    ls.hs.assign(1, h);
+    ls.groups = h->groups;
+    ls.gch = h->gch;
+    ls.owner.assign(h->gch.size(), 0);
+    ls.d_imgs = h->d_imgs;
+    ls.d_gch = h->d_gchains;
+}
+
+// Longest segment <= want, starting after sweep t0, that crosses no
+// problem's refresh boundary.
+int segment_len_at(const bdecon_handle* h, int64_t t0, int want)
+{
+    int len = std::min(want, kMaxSlots);
+    for (const auto& ph : h->probs)
+        if (ph.p.refresh_every > 0)
+            len = (int)std::min<int64_t>(len, (t0 / ph.p.refresh_every + 1) * ph.p.refresh_every - t0);
+    return len;
+}
+
+int segment_len(const bdecon_handle* h, int want)
+{
+    return segment_len_at(h, h->sweeps, want);
+}
+
+// Host bookkeeping of a finished segment: sweep counter and running-mean count.
+void advance_host(bdecon_handle* h, int len)
+{
+    const int64_t t0 = h->sweeps;
+    h->sweeps += len;
+    for (auto& ph : h->probs)
+        for (int64_t t = t0 + 1; t <= t0 + len; ++t)
+            if (t > ph.p.burn_in) ++ph.n_sum;
+}
+
+// After a segment: trace, counters, running-sum bookkeeping, refreshes.
+bdecon_status finish_segment(bdecon_handle* h, int len)
+{
+    launch_trace(h->d_imgs, h->d_chains, (int)h->chains.size(), len, h->st, &h->launches);
+    CK(h, cudaGetLastError());
+    advance_host(h, len);
+    for (auto& ph : h->probs) {
+        if (ph.p.refresh_every > 0 && h->sweeps % ph.p.refresh_every == 0)
+            for (int c = 0; c < ph.p.n_chains; ++c) {
+                const int ci = ph.chain0 + c;
+                bdecon_status s = refresh(h, ci, 1, h->chains[ci].trace, h->chains[ci].tdev);
+                if (s != BDECON_OK) return s;
+            }
+    }
+    return BDECON_OK;
+}
+
+// One segment of len sweeps over every handle of the launch set, on stream st
+// (kernel launches only: each chain starts from its own device sweep
+// counter, so the segment can be captured in a CUDA graph); eh receives
+// errors; gev (optional) gets an event before each group's launch and after
+// the last.
+bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle* eh, cudaEvent_t* gev = nullptr)
+{
+    for (bdecon_handle* h : ls.hs) launch_reset(h->d_imgs, h->d_chains, (int)h->chains.size(), len, st, &h->launches);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (eh->timing) {
+        if (eh->ev_used + 2 > eh->ev_pool.size()) {
+            for (int k = 0; k < 2; ++k) {
+                cudaEvent_t ev;
+                CK(eh, cudaEventCreate(&ev));
+                eh->ev_pool.push_back(ev);
+            }
+        }
+        ev0 = eh->ev_pool[eh->ev_used];
+        ev1 = eh->ev_pool[eh->ev_used + 1];
+        eh->ev_used += 2;
+        CK(eh, cudaEventRecord(ev0, st));
+    }
+    for (size_t gi = 0; gi < ls.groups.size(); ++gi) {
+        const Group& g = ls.groups[gi];
+        if (gev) CK(eh, cudaEventRecord(gev[gi], st));
+        SweepArgs a;
+        a.imgs = ls.d_imgs; a.chains = ls.d_gch + g.chain_off; a.n_chains = g.n_chains;
+        a.n_sweeps = len; a.err = eh->d_err; a.resident = g.resident;
+        a.wait_ns = eh->wait_ns; a.silent_block = gi == 0 ? eh->silent_block : -1;
+        cudaError_t e = eh->precision == BDECON_FP32 ? launch_sweep<float>(a, g.grid, g.threads, g.smem, st)
+                                                     : launch_sweep<double>(a, g.grid, g.threads, g.smem, st);
+        if (e != cudaSuccess)
+            return fail(eh, BDECON_ERR_CUDA, "sweep launch (%d blocks x %d threads, %zu B shared): %s", g.grid,
+                        g.threads, g.smem, cudaGetErrorString(e));
+        ++eh->launches;
+    }
+    if (gev) CK(eh, cudaEventRecord(gev[ls.groups.size()], st));
+    if (eh->timing) CK(eh, cudaEventRecord(ev1, st));
+    for (bdecon_handle* h : ls.hs) {
+        bdecon_status s = finish_segment(h, len);
+        if (s != BDECON_OK) return s;
+    }
+    return BDECON_OK;
+}
+
+// The segment sequence of n sweeps from the current counter: each segment's
+// length, followed by -1-k for each problem k refreshed after it.
+std::vector<int> sweep_signature(const bdecon_handle* h, int n)
+{
+    std::vector<int> sig;
+    int64_t sw = h->sweeps;
+    while (n > 0) {
+        const int len = segment_len_at(h, sw, n);
+        sig.push_back(len);
+        sw += len;
+        for (size_t k = 0; k < h->probs.size(); ++k) {
+            const int re = h->probs[k].p.refresh_every;
+            if (re > 0 && sw % re == 0) sig.push_back(-1 - (int)k);
+        }
+        n -= len;
+    }
+    return sig;
+}
+
+// n sweeps as one CUDA-graph launch: the kernels of every segment (reset,
+// sweep launches, trace, refreshes) are captured once per segment sequence
+// and replayed; the host only advances its counters.
+bdecon_status graph_sweep(bdecon_handle* h, int n)
+{
+    const std::vector<int> sig = sweep_signature(h, n);
+    bdecon_handle::GraphEntry* ge = nullptr;
+    for (auto& g : h->graphs)
+        if (g.sig == sig) ge = &g;
+    if (!ge) {
+        if (!h->cap_st) CK(h, cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+        const int64_t sw0 = h->sweeps, l0 = h->launches;
+        std::vector<int64_t> nsum0;
+        for (const auto& ph : h->probs) nsum0.push_back(ph.n_sum);
+        const cudaStream_t user_st = h->st;
+        const bool timing = h->timing;
+        h->st = h->cap_st;
+        h->timing = false;
+        bdecon_status s = BDECON_OK;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            LaunchSet ls;
+            own_launch_set(h, ls);
+            for (int left = n; left > 0 && s == BDECON_OK;) {
+                const int len = segment_len(h, left);
+                s = run_segment(ls, len, h->cap_st, h);
+                left -= len;
+            }
+            e = cudaStreamEndCapture(h->cap_st, &graph);
+        }
+        h->st = user_st;
+        h->timing = timing;
+        h->sweeps = sw0;
+        for (size_t k = 0; k < h->probs.size(); ++k) h->probs[k].n_sum = nsum0[k];
+        const int64_t nl = h->launches - l0;
+        h->launches = l0;
+        if (s != BDECON_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess) return fail(h, BDECON_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail(h, BDECON_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+        if (h->graphs.size() >= 8) {
+            cudaGraphExecDestroy(h->graphs.front().exec);
+            h->graphs.erase(h->graphs.begin());
+        }
+        h->graphs.push_back({sig, exec, nl});
+        ge = &h->graphs.back();
+    }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (h->timing) {
+        if (h->ev_used + 2 > h->ev_pool.size())
+            for (int k = 0; k < 2; ++k) {
+                cudaEvent_t ev;
+                CK(h, cudaEventCreate(&ev));
+                h->ev_pool.push_back(ev);
+            }
+        ev0 = h->ev_pool[h->ev_used];
+        ev1 = h->ev_pool[h->ev_used + 1];
+        h->ev_used += 2;
+        CK(h, cudaEventRecord(ev0, h->st));
+    }
+    CK(h, cudaGraphLaunch(ge->exec, h->st));
+    if (h->timing) CK(h, cudaEventRecord(ev1, h->st));
+    h->launches += ge->launches;
+    for (int x : sig)
+        if (x > 0) advance_host(h, x);
     return BDECON_OK;
 }
 
@@ -648,6 +928,8 @@ void bdecon_destroy(bdecon_handle* h)
 {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st); else cudaDeviceSynchronize();
+    drop_graphs(h);
+    if (h->cap_st) cudaStreamDestroy(h->cap_st);
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
     if (h->own_arena && h->arena) cudaFree(h->arena);
     delete h;
@@ -666,55 +948,25 @@ bdecon_status bdecon_sweep(bdecon_handle* h, int32_t n)
     if (h->sweeps + n > h->max_sweeps)
         return fail(h, BDECON_ERR_INVALID, "trace capacity %d exceeded (%lld + %d sweeps)", h->max_sweeps,
                     (long long)h->sweeps, n);
+    if (h->use_graph && n > 0) return graph_sweep(h, n);
+    LaunchSet ls;
+    own_launch_set(h, ls);
     while (n > 0) {
-        const int t0 = (int)h->sweeps;
-        int len = std::min(n, kMaxSlots);
-        for (auto& ph : h->probs)
-            if (ph.p.refresh_every > 0) len = std::min(len, (t0 / ph.p.refresh_every + 1) * ph.p.refresh_every - t0);
-        launch_reset(h->d_imgs, h->d_chains, (int)h->chains.size(), len, h->st, &h->launches);
-        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-        if (h->timing) {
-            if (h->ev_used + 2 > h->ev_pool.size()) {
-                for (int k = 0; k < 2; ++k) {
-                    cudaEvent_t ev;
-                    CK(h, cudaEventCreate(&ev));
-                    h->ev_pool.push_back(ev);
-                }
-            }
-            ev0 = h->ev_pool[h->ev_used];
-            ev1 = h->ev_pool[h->ev_used + 1];
-            h->ev_used += 2;
-            CK(h, cudaEventRecord(ev0, h->st));
-        }
-        for (size_t gi = 0; gi < h->groups.size(); ++gi) {
-            const Group& g = h->groups[gi];
-            SweepArgs a;
-            a.imgs = h->d_imgs; a.chains = h->d_gchains + g.chain_off; a.n_chains = g.n_chains;
-            a.t0 = t0; a.n_sweeps = len; a.err = h->d_err; a.resident = g.resident;
-            a.wait_ns = h->wait_ns; a.silent_block = gi == 0 ? h->silent_block : -1;
-            cudaError_t e = h->precision == BDECON_FP32 ? launch_sweep<float>(a, g.grid, g.threads, g.smem, h->st)
-                                                        : launch_sweep<double>(a, g.grid, g.threads, g.smem, h->st);
-            if (e != cudaSuccess)
-                return fail(h, BDECON_ERR_CUDA, "sweep launch (%d blocks x %d threads, %zu B shared): %s", g.grid,
-                            g.threads, g.smem, cudaGetErrorString(e));
-            ++h->launches;
-        }
-        if (h->timing) CK(h, cudaEventRecord(ev1, h->st));
-        launch_trace(h->d_imgs, h->d_chains, (int)h->chains.size(), t0, len, h->st, &h->launches);
-        CK(h, cudaGetLastError());
-        h->sweeps += len;
+        const int len = segment_len(h, n);
+        bdecon_status s = run_segment(ls, len, h->st, h);
+        if (s != BDECON_OK) return s;
         n -= len;
-        for (auto& ph : h->probs) {
-            for (int t = t0 + 1; t <= t0 + len; ++t)
-                if (t > ph.p.burn_in) ++ph.n_sum;
-            if (ph.p.refresh_every > 0 && h->sweeps % ph.p.refresh_every == 0)
-                for (int c = 0; c < ph.p.n_chains; ++c) {
-                    const int ci = ph.chain0 + c;
-                    bdecon_status s = refresh(h, ci, 1, h->chains[ci].trace + h->sweeps);
-                    if (s != BDECON_OK) return s;
-                }
-        }
     }
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_set_graph(bdecon_handle* h, int32_t enable)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    bdecon_status s = check_device(h);
+    if (s != BDECON_OK) return s;
+    h->use_graph = enable != 0;
+    if (!h->use_graph) drop_graphs(h);
     return BDECON_OK;
 }
 
@@ -845,6 +1097,7 @@ bdecon_status bdecon_set_state(bdecon_handle* h, int32_t p, int32_t c, const dou
     else launch_set_rho<double>(h->d_up, h->chains[ci].rho, n, h->st, &h->launches);
     h->sweeps = sweeps;
     // the sweep counter is shared by every chain of the handle: rebase all traces
+    launch_set_counters(h->d_chains, (int)h->chains.size(), (int)sweeps, h->st, &h->launches);
     for (size_t k = 0; k < h->chains.size(); ++k) {
         s = refresh(h, (int)k, 1, h->chains[k].trace + sweeps);
         if (s != BDECON_OK) return s;
@@ -901,14 +1154,17 @@ bdecon_status bdecon_set_plan(bdecon_handle* h, int32_t p, int32_t tile_i, int32
     Group& g = h->groups[h->prob_group[p]];
     const int old_i = ph.tpi, old_j = ph.tpj, old_w = g.warps;
     const bool old_u = ph.user_plan, old_uw = g.user_warps;
-    if (tile_i == 0) {
+    if (tile_i < 0 || tile_j < 0 || warps < 0 || warps > 8) return fail(h, BDECON_ERR_INVALID, "bad plan");
+    if (tile_i == 0 || tile_j == 0) {
         ph.user_plan = false;
-        g.user_warps = false;
     } else {
-        if (tile_i < 1 || tile_j < 1 || warps < 1 || warps > 8) return fail(h, BDECON_ERR_INVALID, "bad plan");
         ph.user_plan = true;
         ph.tpi = std::min(tile_i, ph.npi);
         ph.tpj = std::min(tile_j, ph.npj);
+    }
+    if (warps == 0) {
+        g.user_warps = false;
+    } else {
         g.warps = warps;
         g.user_warps = true;
     }
@@ -920,6 +1176,167 @@ bdecon_status bdecon_set_plan(bdecon_handle* h, int32_t p, int32_t tile_i, int32
         make_plan(h);
         h->err = m;
     }
+    return s;
+}
+
+bdecon_status bdecon_set_grouping(bdecon_handle* h, int32_t one_launch)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    bdecon_status s = check_device(h);
+    if (s != BDECON_OK) return s;
+    const bool old = h->one_launch;
+    const std::vector<Group> old_groups = h->groups;
+    const std::vector<int> old_pg = h->prob_group;
+    h->one_launch = one_launch != 0;
+    form_groups(h);
+    s = make_plan(h);
+    if (s != BDECON_OK) {
+        const std::string m = h->err;
+        h->one_launch = old;
+        h->groups = old_groups;
+        h->prob_group = old_pg;
+        make_plan(h);
+        h->err = m;
+    }
+    return s;
+}
+
+namespace {
+
+// One autotuner trial: a segment of len sweeps in the current plan, timed
+// per launch group.  Returns the per-group milliseconds (or an error).
+bdecon_status tune_trial(bdecon_handle* h, int len, std::vector<double>& ms)
+{
+    const size_t ng = h->groups.size();
+    std::vector<cudaEvent_t> ev(ng + 1);
+    for (auto& e : ev) CK(h, cudaEventCreate(&e));
+    LaunchSet ls;
+    own_launch_set(h, ls);
+    bdecon_status s = run_segment(ls, len, h->st, h, ev.data());
+    if (s == BDECON_OK) s = check_device(h);
+    ms.assign(ng, 0.0);
+    if (s == BDECON_OK)
+        for (size_t g = 0; g < ng; ++g) {
+            float t = 0;
+            cudaEventElapsedTime(&t, ev[g], ev[g + 1]);
+            ms[g] = t;
+        }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return s;
+}
+
+struct TuneChoice {
+    int warps = 0;          // 0: the team's own
+    bool streamed = false;
+    double ms = 1e300;
+};
+
+}  // namespace
+
+bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* one_launch, double* ms_per_sweep)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    if (h->failed) return fail(h, BDECON_ERR_STATE, "handle failed earlier: %s", h->err.c_str());
+    if (trial_sweeps < 1 || trial_sweeps > kMaxSlots) return fail(h, BDECON_ERR_INVALID, "trial_sweeps must be 1..%d", kMaxSlots);
+    if (h->sweeps + trial_sweeps > h->max_sweeps)
+        return fail(h, BDECON_ERR_INVALID, "trace capacity %d too small for %d trial sweeps after %lld", h->max_sweeps,
+                    trial_sweeps, (long long)h->sweeps);
+    bdecon_status s = check_device(h);
+    if (s != BDECON_OK) return s;
+    // snapshot: the whole workspace on the device, the counters on the host
+    char* snap = nullptr;
+    if (cudaMalloc(&snap, h->arena_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, BDECON_ERR_NOMEM, "autotune needs a %zu-byte copy of the workspace", h->arena_bytes);
+    }
+    CK(h, cudaMemcpyAsync(snap, h->arena, h->arena_bytes, cudaMemcpyDeviceToDevice, h->st));
+    const int64_t sweeps0 = h->sweeps;
+    std::vector<int64_t> nsum0;
+    for (const auto& ph : h->probs) nsum0.push_back(ph.n_sum);
+    auto restore = [&]() -> bdecon_status {
+        CK(h, cudaMemcpyAsync(h->arena, snap, h->arena_bytes, cudaMemcpyDeviceToDevice, h->st));
+        CK(h, cudaStreamSynchronize(h->st));
+        h->sweeps = sweeps0;
+        for (size_t k = 0; k < h->probs.size(); ++k) h->probs[k].n_sum = nsum0[k];
+        return BDECON_OK;
+    };
+    const int len = std::min<int>(trial_sweeps, segment_len(h, trial_sweeps));
+    for (auto& ph : h->probs) ph.user_plan = false;
+    static const int kMult[3] = {1, 2, 4};
+    // (a) one launch per (L, S, team): each group's warps and residency tuned on its own
+    h->one_launch = false;
+    form_groups(h);
+    std::vector<TuneChoice> best(h->groups.size());
+    for (int streamed = 0; streamed <= 1 && s == BDECON_OK; ++streamed)
+        for (int mi = 0; mi < 3 && s == BDECON_OK; ++mi) {
+            bool any = false;
+            for (auto& g : h->groups) {
+                const int tw = g.team / 32, w = std::min(8, tw * kMult[mi]);
+                any = any || (mi == 0 || w != std::min(8, tw * kMult[mi - 1]));
+                g.warps = w;
+                g.user_warps = true;
+                g.streamed = streamed != 0;
+            }
+            if (!any) continue;
+            if (make_plan(h) != BDECON_OK) continue;   // no co-resident plan of this shape
+            std::vector<double> ms;
+            s = tune_trial(h, len, ms);
+            if (s == BDECON_OK) s = restore();
+            for (size_t g = 0; g < ms.size() && s == BDECON_OK; ++g)
+                if (ms[g] < best[g].ms) best[g] = {h->groups[g].warps, streamed != 0, ms[g]};
+        }
+    double t_groups = 0;
+    for (const auto& b : best) t_groups += b.ms;
+    // (b) one launch over every problem
+    TuneChoice one;
+    if (s == BDECON_OK && h->probs.size() > 1) {
+        h->one_launch = true;
+        form_groups(h);
+        Group& g = h->groups[0];
+        bool behind = false;   // the first shapes are far slower than per-group launches: stop trying
+        for (int streamed = 0; streamed <= 1 && s == BDECON_OK && !behind; ++streamed)
+            for (int mi = 0; mi < 3 && s == BDECON_OK && !behind; ++mi) {
+                const int w = std::min(8, (g.team / 32) * kMult[mi]);
+                if (mi > 0 && w == std::min(8, (g.team / 32) * kMult[mi - 1])) continue;
+                g.warps = w;
+                g.user_warps = true;
+                g.streamed = streamed != 0;
+                if (make_plan(h) != BDECON_OK) continue;
+                std::vector<double> ms;
+                s = tune_trial(h, len, ms);
+                if (s == BDECON_OK) s = restore();
+                if (s == BDECON_OK && ms[0] < one.ms) one = {w, streamed != 0, ms[0]};
+                behind = s == BDECON_OK && one.ms > 1.5 * t_groups;
+            }
+    }
+    // apply the fastest
+    if (s == BDECON_OK) {
+        h->one_launch = one.ms < t_groups;
+        form_groups(h);
+        if (h->one_launch) {
+            h->groups[0].warps = one.warps;
+            h->groups[0].user_warps = true;
+            h->groups[0].streamed = one.streamed;
+        } else {
+            for (size_t g = 0; g < h->groups.size(); ++g) {
+                h->groups[g].warps = best[g].warps;
+                h->groups[g].user_warps = true;
+                h->groups[g].streamed = best[g].streamed;
+            }
+        }
+        s = make_plan(h);
+        if (one_launch) *one_launch = h->one_launch ? 1 : 0;
+        if (ms_per_sweep) *ms_per_sweep = (h->one_launch ? one.ms : t_groups) / len;
+    }
+    if (s != BDECON_OK) {
+        const std::string m = h->err;
+        restore();
+        h->one_launch = false;
+        form_groups(h);
+        make_plan(h);
+        h->err = m;
+    }
+    cudaFree(snap);
     return s;
 }
 
@@ -950,6 +1367,7 @@ bdecon_status bdecon_set_fault(bdecon_handle* h, int32_t silent_block, int64_t w
     if (wait_ns < 1000000 || wait_ns > 60000000000ll) return fail(h, BDECON_ERR_INVALID, "wait limit out of range");
     h->silent_block = silent_block < 0 ? -1 : silent_block;
     h->wait_ns = (unsigned long long)wait_ns;
+    drop_graphs(h);   // captured launches carry the old values
     return BDECON_OK;
 }
 
@@ -973,6 +1391,426 @@ bdecon_status bdecon_sweep_kernel_time(bdecon_handle* h, double* ms, int64_t* la
     *ms = tot;
     *launches = (int64_t)(h->ev_used / 2);
     h->ev_used = 0;
+    return BDECON_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ serving
+// Continuous batching: a worker thread admits queued jobs when a slot and
+// device memory are free, sweeps every running job in shared cooperative
+// launches (one per (L, S, team) across jobs, or one in all) per segment of
+// at most segment_sweeps sweeps, and between segments retires finished jobs (their
+// posterior mean is kept for polling) and admits new ones.  A job's chains
+// keep their own sweep counter, refresh schedule and random stream, so its
+// result does not depend on what else runs with it.
+namespace {
+
+struct SrvJob {
+    int64_t id = 0;
+    std::vector<float> image, gain, offset, var;
+    std::vector<double> psf;
+    bdecon_problem p{};
+    int sweeps = 0, remaining = 0;
+    int state = BDECON_JOB_QUEUED;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    size_t mem = 0;
+    bdecon_handle* h = nullptr;
+    std::vector<double> mean;
+    std::string err;
+};
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct bdecon_server {
+    bdecon_server_config cfg{};
+    cudaStream_t st = nullptr;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    std::deque<int64_t> queue;
+    std::map<int64_t, SrvJob*> jobs;
+    std::vector<SrvJob*> active;        // worker-thread only
+    size_t mem_used = 0;
+    int64_t next_id = 1;
+    int64_t segments = 0;
+    char* d_tab = nullptr;              // device tables of the shared launches
+    size_t tab_cap = 0;
+    bdecon_handle shell;                // error flag, precision, launch counter of the shared launches
+    std::string err;
+};
+
+namespace {
+
+bool srv_tables(bdecon_server* S, size_t bytes)
+{
+    if (bytes <= S->tab_cap) return true;
+    if (S->d_tab) cudaFree(S->d_tab);
+    S->d_tab = nullptr;
+    S->tab_cap = 0;
+    const size_t cap = std::max(bytes, (size_t)1 << 16);
+    if (cudaMalloc(&S->d_tab, cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    S->tab_cap = cap;
+    return true;
+}
+
+// Build the shared launch over the running jobs: a combined image table,
+// one group per (L, S, team), chain copies in group order.
+bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
+{
+    ls = LaunchSet();
+    imgs.clear();
+    struct Entry { int hi, pk, img; };
+    std::vector<Entry> ent;
+    for (size_t hi = 0; hi < S->active.size(); ++hi) {
+        bdecon_handle* h = S->active[hi]->h;
+        ls.hs.push_back(h);
+        for (size_t k = 0; k < h->probs.size(); ++k) {
+            ent.push_back({(int)hi, (int)k, (int)imgs.size()});
+            imgs.push_back(h->imgs[k]);
+        }
+    }
+    // One launch per (L, S, team) across jobs, or one launch over every
+    // running job (the kernel reads each block's problem from its chain).
+    std::vector<std::vector<int>> groups;   // indices into ent
+    for (size_t e = 0; e < ent.size(); ++e) {
+        const bdecon_handle* h = ls.hs[ent[e].hi];
+        const ProbHost& ph = h->probs[ent[e].pk];
+        const int team = h->imgs[ent[e].pk].team;
+        int gi = -1;
+        for (size_t q = 0; q < groups.size() && gi < 0; ++q) {
+            const Entry& f = ent[groups[q][0]];
+            const bdecon_handle* h2 = ls.hs[f.hi];
+            if (S->cfg.one_launch ||
+                (h2->probs[f.pk].L == ph.L && h2->probs[f.pk].S == ph.S && h2->imgs[f.pk].team == team))
+                gi = (int)q;
+        }
+        if (gi < 0) {
+            groups.emplace_back();
+            gi = (int)groups.size() - 1;
+        }
+        groups[gi].push_back((int)e);
+    }
+    // chain copies (img remapped), planned per group, laid out in group order
+    std::vector<Chain> all;
+    std::vector<int> all_owner, first(ent.size());
+    for (size_t e = 0; e < ent.size(); ++e) {
+        const bdecon_handle* h = ls.hs[ent[e].hi];
+        const ProbHost& ph = h->probs[ent[e].pk];
+        first[e] = (int)all.size();
+        for (int c = 0; c < ph.p.n_chains; ++c) {
+            Chain ch = h->chains[ph.chain0 + c];
+            ch.img = ent[e].img;
+            all.push_back(ch);
+            all_owner.push_back(ent[e].hi);
+        }
+    }
+    for (auto& gidx : groups) {
+        Group g;
+        std::vector<PlanItem> items(gidx.size());
+        std::vector<PlanItem*> ptrs;
+        for (size_t q = 0; q < gidx.size(); ++q) {
+            const Entry& e = ent[gidx[q]];
+            const bdecon_handle* h = ls.hs[e.hi];
+            PlanItem& it = items[q];
+            it.ph = &h->probs[e.pk];
+            it.team = h->imgs[e.pk].team;
+            for (int c = 0; c < it.ph->p.n_chains; ++c) it.chains.push_back(&all[first[gidx[q]] + c]);
+            ptrs.push_back(&it);
+        }
+        std::string err;
+        if (!plan_items(S->shell.precision, S->shell.sms, ptrs, g, err)) {
+            S->err = err;
+            return false;
+        }
+        g.chain_off = (int)ls.gch.size();
+        for (size_t q = 0; q < gidx.size(); ++q) {
+            const Entry& e = ent[gidx[q]];
+            for (int c = 0; c < ls.hs[e.hi]->probs[e.pk].p.n_chains; ++c) {
+                ls.gch.push_back(all[first[gidx[q]] + c]);
+                ls.owner.push_back(all_owner[first[gidx[q]] + c]);
+            }
+        }
+        g.n_chains = (int)ls.gch.size() - g.chain_off;
+        ls.groups.push_back(g);
+    }
+    const size_t bi = sizeof(Image) * imgs.size(), bc = sizeof(Chain) * ls.gch.size();
+    if (!srv_tables(S, align_up(bi, 256) + bc + 256)) {
+        S->err = "cudaMalloc of the launch tables failed";
+        return false;
+    }
+    if (cudaMemcpyAsync(S->d_tab, imgs.data(), bi, cudaMemcpyHostToDevice, S->st) != cudaSuccess) {
+        S->err = "launch table upload failed";
+        return false;
+    }
+    ls.d_imgs = (const Image*)S->d_tab;
+    ls.d_gch = (Chain*)(S->d_tab + align_up(bi, 256));
+    if (cudaMemcpyAsync(ls.d_gch, ls.gch.data(), bc, cudaMemcpyHostToDevice, S->st) != cudaSuccess) {
+        S->err = "launch table upload failed";
+        return false;
+    }
+    return true;
+}
+
+void srv_finish(bdecon_server* S, SrvJob* j, int state, std::string err)   // err by value: it may live in j->h
+{
+    if (j->h) {
+        bdecon_destroy(j->h);
+        j->h = nullptr;
+    }
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->mem_used -= j->mem;
+    j->state = state;
+    j->err = std::move(err);
+    j->t_done = now_s();
+    S->cv.notify_all();
+}
+
+void srv_loop(bdecon_server* S)
+{
+    cudaSetDevice(S->cfg.device);
+    LaunchSet ls;
+    std::vector<Image> imgs;
+    bool dirty = true;
+    for (;;) {
+        std::vector<SrvJob*> admit;
+        {
+            std::unique_lock<std::mutex> lock(S->mu);
+            if (S->active.empty() && S->queue.empty() && !S->stop)
+                S->cv.wait_for(lock, std::chrono::milliseconds(20));
+            if (S->stop) break;
+            while (!S->queue.empty() && (int)(S->active.size() + admit.size()) < S->cfg.max_jobs) {
+                SrvJob* j = S->jobs[S->queue.front()];
+                if (S->mem_used + j->mem > S->cfg.mem_budget) break;   // wait for memory to free up
+                S->queue.pop_front();
+                S->mem_used += j->mem;
+                admit.push_back(j);
+            }
+        }
+        for (SrvJob* j : admit) {
+            bdecon_status st = bdecon_create(&j->p, S->st, &j->h);
+            if (st != BDECON_OK) {
+                j->h = nullptr;
+                srv_finish(S, j, BDECON_JOB_FAILED, bdecon_last_error(nullptr));
+                continue;
+            }
+            {
+                std::lock_guard<std::mutex> lock(S->mu);
+                j->state = BDECON_JOB_RUNNING;
+                j->t_start = now_s();
+            }
+            S->active.push_back(j);
+            dirty = true;
+        }
+        if (S->active.empty()) continue;
+        if (dirty) {
+            if (!srv_build(S, ls, imgs)) {
+                for (SrvJob* j : S->active) srv_finish(S, j, BDECON_JOB_FAILED, S->err);
+                S->active.clear();
+                continue;
+            }
+            dirty = false;
+        }
+        int len = S->cfg.segment_sweeps;
+        for (SrvJob* j : S->active) len = std::min(len, segment_len(j->h, j->remaining));
+        bdecon_status st = run_segment(ls, len, S->st, &S->shell);
+        if (st == BDECON_OK) st = check_device(&S->shell);
+        if (st != BDECON_OK) {
+            const std::string m = S->shell.err;
+            for (SrvJob* j : S->active) srv_finish(S, j, BDECON_JOB_FAILED, m);
+            S->active.clear();
+            cudaMemsetAsync(S->shell.d_err, 0, sizeof(int), S->st);
+            S->shell.failed = false;
+            dirty = true;
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            ++S->segments;
+        }
+        std::vector<SrvJob*> keep;
+        for (SrvJob* j : S->active) {
+            j->remaining -= len;
+            if (j->remaining > 0) {
+                keep.push_back(j);
+                continue;
+            }
+            const ProbHost& ph = j->h->probs[0];
+            j->mean.assign((size_t)ph.Ho * ph.Wo, 0.0);
+            if (bdecon_posterior_mean(j->h, 0, j->mean.data(), 0) != BDECON_OK) {
+                srv_finish(S, j, BDECON_JOB_FAILED, j->h->err);
+            } else {
+                srv_finish(S, j, BDECON_JOB_DONE, "");
+            }
+            dirty = true;
+        }
+        S->active.swap(keep);
+    }
+    for (SrvJob* j : S->active) srv_finish(S, j, BDECON_JOB_FAILED, "server stopped");
+    S->active.clear();
+}
+
+}  // namespace
+
+extern "C" {
+
+bdecon_status bdecon_server_start(const bdecon_server_config* cfg, bdecon_server** out)
+{
+    if (!cfg || !out) return fail(nullptr, BDECON_ERR_INVALID, "bad arguments");
+    *out = nullptr;
+    if (cfg->max_jobs < 1 || cfg->segment_sweeps < 1 || cfg->segment_sweeps > kMaxSlots || cfg->mem_budget == 0 ||
+        (cfg->precision != BDECON_FP32 && cfg->precision != BDECON_FP64))
+        return fail(nullptr, BDECON_ERR_INVALID, "server config out of range");
+    bdecon_server* S = new bdecon_server();
+    S->cfg = *cfg;
+    if (cudaSetDevice(cfg->device) != cudaSuccess || cudaStreamCreateWithFlags(&S->st, cudaStreamNonBlocking) != cudaSuccess) {
+        delete S;
+        return fail(nullptr, BDECON_ERR_CUDA, "cannot use device %d", cfg->device);
+    }
+    S->shell.precision = cfg->precision;
+    S->shell.st = S->st;
+    cudaDeviceGetAttribute(&S->shell.sms, cudaDevAttrMultiProcessorCount, cfg->device);
+    if (cudaMalloc(&S->shell.d_err, 256) != cudaSuccess || cudaMemset(S->shell.d_err, 0, 256) != cudaSuccess) {
+        cudaStreamDestroy(S->st);
+        delete S;
+        return fail(nullptr, BDECON_ERR_NOMEM, "server error flag");
+    }
+    S->worker = std::thread(srv_loop, S);
+    *out = S;
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_server_submit(bdecon_server* S, const bdecon_problem* p, int32_t sweeps, int64_t* job_id)
+{
+    if (!S || !p || !job_id) return fail(nullptr, BDECON_ERR_INVALID, "bad arguments");
+    if (sweeps < 1) return fail(nullptr, BDECON_ERR_INVALID, "sweeps must be >= 1");
+    if (sweeps <= p->burn_in)
+        return fail(nullptr, BDECON_ERR_INVALID, "sweeps (%d) must exceed burn_in (%d): the job returns a posterior mean",
+                    sweeps, p->burn_in);
+    if (p->precision != S->cfg.precision) return fail(nullptr, BDECON_ERR_INVALID, "job precision differs from the server's");
+    bdecon_status st = validate(*p, 0);
+    if (st != BDECON_OK) return st;
+    SrvJob* j = new SrvJob();
+    const size_t n = (size_t)p->H * p->W;
+    j->image.assign(p->image, p->image + n);
+    if (p->gain_map) j->gain.assign(p->gain_map, p->gain_map + n);
+    if (p->offset_map) j->offset.assign(p->offset_map, p->offset_map + n);
+    if (p->var_map) j->var.assign(p->var_map, p->var_map + n);
+    j->psf.assign(p->psf, p->psf + (size_t)p->L * p->L);
+    j->p = *p;
+    j->p.image = j->image.data();
+    j->p.gain_map = p->gain_map ? j->gain.data() : nullptr;
+    j->p.offset_map = p->offset_map ? j->offset.data() : nullptr;
+    j->p.var_map = p->var_map ? j->var.data() : nullptr;
+    j->p.psf = j->psf.data();
+    j->p.max_sweeps = sweeps;
+    j->p.flags = 0;
+    j->sweeps = j->remaining = sweeps;
+    size_t bytes = 0;
+    st = bdecon_workspace_size(&j->p, 1, &bytes);
+    if (st != BDECON_OK) {
+        delete j;
+        return st;
+    }
+    j->mem = bytes;
+    j->t_submit = now_s();
+    std::lock_guard<std::mutex> lock(S->mu);
+    j->id = S->next_id++;
+    S->jobs[j->id] = j;
+    if (j->mem > S->cfg.mem_budget) {
+        j->state = BDECON_JOB_FAILED;
+        j->err = "job needs more device memory than the server budget";
+        j->t_done = j->t_submit;
+    } else {
+        S->queue.push_back(j->id);
+    }
+    *job_id = j->id;
+    S->cv.notify_all();
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_server_poll(bdecon_server* S, int64_t id, int32_t* state, double* times, double* mean, size_t cap)
+{
+    if (!S || !state) return fail(nullptr, BDECON_ERR_INVALID, "bad arguments");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->jobs.find(id);
+    if (it == S->jobs.end()) return fail(nullptr, BDECON_ERR_INVALID, "unknown job %lld", (long long)id);
+    SrvJob* j = it->second;
+    *state = j->state;
+    if (times) {
+        times[0] = j->t_submit;
+        times[1] = j->t_start;
+        times[2] = j->t_done;
+    }
+    if (j->state == BDECON_JOB_FAILED) return fail(nullptr, BDECON_ERR_STATE, "job failed: %s", j->err.c_str());
+    if (mean && j->state == BDECON_JOB_DONE) {
+        if (cap < j->mean.size()) return fail(nullptr, BDECON_ERR_INVALID, "output capacity %zu < %zu", cap, j->mean.size());
+        std::memcpy(mean, j->mean.data(), j->mean.size() * sizeof(double));
+    }
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_server_wait(bdecon_server* S, int64_t id, double timeout_s, int32_t* state)
+{
+    if (!S || !state) return fail(nullptr, BDECON_ERR_INVALID, "bad arguments");
+    std::unique_lock<std::mutex> lock(S->mu);
+    auto it = S->jobs.find(id);
+    if (it == S->jobs.end()) return fail(nullptr, BDECON_ERR_INVALID, "unknown job %lld", (long long)id);
+    SrvJob* j = it->second;
+    S->cv.wait_for(lock, std::chrono::duration<double>(timeout_s),
+                   [&] { return j->state == BDECON_JOB_DONE || j->state == BDECON_JOB_FAILED; });
+    *state = j->state;
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_server_stats(bdecon_server* S, int64_t* queued, int64_t* running, int64_t* done, size_t* mem_used,
+                                  int64_t* segments)
+{
+    if (!S) return fail(nullptr, BDECON_ERR_INVALID, "server is NULL");
+    std::lock_guard<std::mutex> lock(S->mu);
+    int64_t q = 0, r = 0, d = 0;
+    for (auto& kv : S->jobs) {
+        q += kv.second->state == BDECON_JOB_QUEUED;
+        r += kv.second->state == BDECON_JOB_RUNNING;
+        d += kv.second->state == BDECON_JOB_DONE;
+    }
+    if (queued) *queued = q;
+    if (running) *running = r;
+    if (done) *done = d;
+    if (mem_used) *mem_used = S->mem_used;
+    if (segments) *segments = S->segments;
+    return BDECON_OK;
+}
+
+bdecon_status bdecon_server_stop(bdecon_server* S)
+{
+    if (!S) return fail(nullptr, BDECON_ERR_INVALID, "server is NULL");
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+        for (int64_t id : S->queue) {
+            S->jobs[id]->state = BDECON_JOB_FAILED;
+            S->jobs[id]->err = "server stopped";
+        }
+        S->queue.clear();
+        S->cv.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    cudaStreamSynchronize(S->st);
+    for (auto& kv : S->jobs) delete kv.second;
+    if (S->d_tab) cudaFree(S->d_tab);
+    if (S->shell.d_err) cudaFree(S->shell.d_err);
+    cudaStreamDestroy(S->st);
+    delete S;
     return BDECON_OK;
 }
 

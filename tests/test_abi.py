@@ -98,3 +98,15 @@ def test_workspace_size_grows_with_chains():
     b = bdecon.Sampler.workspace_size(prob)
     assert b > a > 30 * 31 * 4
     assert a % 256 == 0
+
+
+@pytest.mark.parametrize("field,value", [("max_jobs", 0), ("segment_sweeps", 0), ("segment_sweeps", 65),
+                                         ("mem_budget", 0), ("precision", 5)])
+def test_bad_server_config_refused(field, value):
+    L = bdecon.load()
+    cfg = bdecon._ServerConfig(1 << 30, 4, 8, bdecon.BDECON_FP32, 0, 0)
+    setattr(cfg, field, value)
+    s = C.c_void_p()
+    assert L.bdecon_server_start(C.byref(cfg), C.byref(s)) == 1
+    assert s.value is None
+    assert "server config" in L.bdecon_last_error(None).decode()

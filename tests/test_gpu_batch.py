@@ -71,3 +71,84 @@ def test_batch_fp64_matches_oracle():
             np.testing.assert_allclose(rho, ref["rho"], rtol=1e-12)
             np.testing.assert_allclose(b.trace(p, c), ref["trace"], rtol=1e-12)
     b.close()
+
+
+@pytest.mark.parametrize("precision", [bdecon.BDECON_FP64, bdecon.BDECON_FP32])
+def test_one_launch_and_autotuned_plans_are_bit_identical(precision):
+    # every problem in one launch (block = the largest team), and the plan the
+    # autotuner picks after timing its trials (the trials' sweeps are undone)
+    probs = _mix()
+    T = 9
+    ref = bdecon.Sampler(probs, precision=precision, max_sweeps=T + 8)
+    ref.sweep(T)
+    want = [_collect(ref, p, pr.n_chains) for p, pr in enumerate(probs)]
+    ref.close()
+
+    one = bdecon.Sampler(probs, precision=precision, max_sweeps=T + 8)
+    one.set_grouping(True)
+    plans = [one.get_plan(p) for p in range(len(probs))]
+    assert len({pl["blocks"] for pl in plans}) == 1 and len({pl["warps"] for pl in plans}) == 1
+    one.sweep(4)
+    one.set_grouping(False)                 # regrouping between sweeps changes nothing either
+    one.sweep(T - 4)
+    got_one = [_collect(one, p, pr.n_chains) for p, pr in enumerate(probs)]
+    one.close()
+
+    tuned = bdecon.Sampler(probs, precision=precision, max_sweeps=T + 8)
+    tuned.sweep(2)
+    info = tuned.autotune(trial_sweeps=3)
+    assert info["ms_per_sweep"] > 0
+    rho, t = tuned.get_state(0, 0)
+    assert t == 2
+    assert tuned.trace(0, 0).size == 2
+    tuned.sweep(T - 2)
+    got_tuned = [_collect(tuned, p, pr.n_chains) for p, pr in enumerate(probs)]
+    tuned.close()
+
+    for got in (got_one, got_tuned):
+        for p, pr in enumerate(probs):
+            for c in range(pr.n_chains):
+                for x, y in zip(got[p][0][c], want[p][0][c]):
+                    np.testing.assert_array_equal(x, y)
+            np.testing.assert_array_equal(got[p][1], want[p][1])
+
+
+def test_warps_only_plan_override():
+    probs = _mix()
+    s = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=8)
+    auto = s.get_plan(3)
+    s.set_plan(0, 0, 8, p=3)                 # automatic tiles, 8 warps for the L = 11 group
+    pl = s.get_plan(3)
+    assert pl["warps"] == 8 and auto["warps"] < 8
+    with pytest.raises(bdecon.BdeconError):
+        s.set_plan(0, 0, 9, p=3)
+    assert s.get_plan(3) == pl                # a refused plan keeps the previous one
+    s.set_plan(0, 0, 0, p=3)
+    assert s.get_plan(3) == auto
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [bdecon.BDECON_FP64, bdecon.BDECON_FP32])
+def test_graph_mode_is_bit_identical(precision):
+    # sweep calls of 3 and 5 sweeps across refreshes every 4 sweeps: the
+    # segment sequences repeat, so later calls replay captured graphs
+    probs = _mix()
+    calls = [3, 5, 3, 5, 2]
+    ref = bdecon.Sampler(probs, precision=precision, max_sweeps=32)
+    for n in calls:
+        ref.sweep(n)
+    want = [_collect(ref, p, pr.n_chains) for p, pr in enumerate(probs)]
+    want_launches = ref.launch_count()
+    ref.close()
+    g = bdecon.Sampler(probs, precision=precision, max_sweeps=32)
+    g.set_graph(True)
+    for n in calls:
+        g.sweep(n)
+    got = [_collect(g, p, pr.n_chains) for p, pr in enumerate(probs)]
+    assert g.launch_count() == want_launches
+    g.close()
+    for p, pr in enumerate(probs):
+        for c in range(pr.n_chains):
+            for x, y in zip(got[p][0][c], want[p][0][c]):
+                np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(got[p][1], want[p][1])
