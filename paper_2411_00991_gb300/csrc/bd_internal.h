@@ -74,13 +74,14 @@ struct Chain {
     int tpi, tpj, nti, ntj;          // tile shape (patches) and tile grid
     int cta_base;                    // first block of this chain in the sweep grid
     int* tdev;                       // sweeps this chain has completed (device counter, advanced by k_trace)
+    int n_sweeps;                    // sweeps of this chain in the launch (0: the launch's n_sweeps)
 };
 
 struct SweepArgs {
     const Image* imgs;
     const Chain* chains;
     int n_chains;
-    int n_sweeps;                    // sweeps in this launch
+    int n_sweeps;                    // sweeps in this launch (chains may take fewer)
     int* err;
     int resident;                    // 1: tile state (data, spectra, rho) held in shared memory
     unsigned long long wait_ns;      // limit of each neighbour wait

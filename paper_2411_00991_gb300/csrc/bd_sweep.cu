@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     T* red1 = red + (size_t)(g * 8) * 4;                   // prior partials of this sub-team
     T* red2 = red + 8 * 8 * 4 + (size_t)(g * 8) * 4;       // likelihood partials
     const T step = (T)im.step;
-    const int nsteps = a.n_sweeps * S2;
+    const int nsteps = (ch.n_sweeps > 0 ? ch.n_sweeps : a.n_sweeps) * S2;
     int n_acc = 0;
     // with one update per team and step, a warp of the team draws the next
     // step's proposal ahead of time (before the neighbour wait); not when a

@@ -739,10 +739,15 @@ bdecon_status finish_segment(bdecon_handle* h, int len)
 // (kernel launches only: each chain starts from its own device sweep
 // counter, so the segment can be captured in a CUDA graph); eh receives
 // errors; gev (optional) gets an event before each group's launch and after
-// the last.
-bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle* eh, cudaEvent_t* gev = nullptr)
+// the last.  lens (optional): sweeps of each handle's chains, at most len;
+// the chain table must then carry them (Chain::n_sweeps).
+bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle* eh, cudaEvent_t* gev = nullptr,
+                          const int* lens = nullptr)
 {
-    for (bdecon_handle* h : ls.hs) launch_reset(h->d_imgs, h->d_chains, (int)h->chains.size(), len, st, &h->launches);
+    for (size_t hi = 0; hi < ls.hs.size(); ++hi) {
+        bdecon_handle* h = ls.hs[hi];
+        launch_reset(h->d_imgs, h->d_chains, (int)h->chains.size(), lens ? lens[hi] : len, st, &h->launches);
+    }
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (eh->timing) {
         if (eh->ev_used + 2 > eh->ev_pool.size()) {
@@ -773,8 +778,8 @@ bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle
     }
     if (gev) CK(eh, cudaEventRecord(gev[ls.groups.size()], st));
     if (eh->timing) CK(eh, cudaEventRecord(ev1, st));
-    for (bdecon_handle* h : ls.hs) {
-        bdecon_status s = finish_segment(h, len);
+    for (size_t hi = 0; hi < ls.hs.size(); ++hi) {
+        bdecon_status s = finish_segment(ls.hs[hi], lens ? lens[hi] : len);
         if (s != BDECON_OK) return s;
     }
     return BDECON_OK;
@@ -1437,6 +1442,8 @@ struct bdecon_server {
     std::deque<int64_t> queue;
     std::map<int64_t, SrvJob*> jobs;
     std::vector<SrvJob*> active;        // worker-thread only
+    std::vector<int> job_group;         // per running job: its launch group
+    std::vector<int64_t> job_cost;      // per running job: class steps x rounds per sweep of its blocks
     size_t mem_used = 0;
     int64_t next_id = 1;
     int64_t segments = 0;
@@ -1543,6 +1550,21 @@ bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
         g.n_chains = (int)ls.gch.size() - g.chain_off;
         ls.groups.push_back(g);
     }
+    // per job: its group and the serial work of one sweep of its blocks
+    // (class steps x patch rounds per team), which sets its sweeps per segment
+    S->job_group.assign(ls.hs.size(), 0);
+    S->job_cost.assign(ls.hs.size(), 1);
+    for (size_t gi = 0; gi < ls.groups.size(); ++gi) {
+        const Group& g = ls.groups[gi];
+        for (int k = g.chain_off; k < g.chain_off + g.n_chains; ++k) {
+            const Chain& ch = ls.gch[k];
+            const Image& im = imgs[ch.img];
+            const int n_sub = std::max(1, g.threads / im.team);
+            const int rounds = (ch.tpi * ch.tpj + n_sub - 1) / n_sub;
+            S->job_group[ls.owner[k]] = (int)gi;
+            S->job_cost[ls.owner[k]] = (int64_t)im.S * im.S * rounds;
+        }
+    }
     const size_t bi = sizeof(Image) * imgs.size(), bc = sizeof(Chain) * ls.gch.size();
     if (!srv_tables(S, align_up(bi, 256) + bc + 256)) {
         S->err = "cudaMalloc of the launch tables failed";
@@ -1554,10 +1576,6 @@ bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
     }
     ls.d_imgs = (const Image*)S->d_tab;
     ls.d_gch = (Chain*)(S->d_tab + align_up(bi, 256));
-    if (cudaMemcpyAsync(ls.d_gch, ls.gch.data(), bc, cudaMemcpyHostToDevice, S->st) != cudaSuccess) {
-        S->err = "launch table upload failed";
-        return false;
-    }
     return true;
 }
 
@@ -1620,9 +1638,29 @@ void srv_loop(bdecon_server* S)
             }
             dirty = false;
         }
-        int len = S->cfg.segment_sweeps;
-        for (SrvJob* j : S->active) len = std::min(len, segment_len(j->h, j->remaining));
-        bdecon_status st = run_segment(ls, len, S->st, &S->shell);
+        // sweeps per job in this segment: the slowest job of each launch group
+        // takes segment_sweeps, lighter ones proportionally more (capped by the
+        // slot count, their next refresh and what they have left), so the
+        // group's blocks finish together and small jobs finish early
+        std::vector<int64_t> gmax(ls.groups.size(), 1);
+        for (size_t hi = 0; hi < S->active.size(); ++hi)
+            gmax[S->job_group[hi]] = std::max(gmax[S->job_group[hi]], S->job_cost[hi]);
+        std::vector<int> lens(S->active.size());
+        int len = 1;
+        for (size_t hi = 0; hi < S->active.size(); ++hi) {
+            const int64_t want = (int64_t)S->cfg.segment_sweeps * gmax[S->job_group[hi]] / S->job_cost[hi];
+            lens[hi] = segment_len(S->active[hi]->h, (int)std::min<int64_t>({want, (int64_t)kMaxSlots,
+                                                                             (int64_t)S->active[hi]->remaining}));
+            len = std::max(len, lens[hi]);
+        }
+        for (size_t k = 0; k < ls.gch.size(); ++k) ls.gch[k].n_sweeps = lens[ls.owner[k]];
+        bdecon_status st = BDECON_OK;
+        if (cudaMemcpyAsync(ls.d_gch, ls.gch.data(), sizeof(Chain) * ls.gch.size(), cudaMemcpyHostToDevice, S->st) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            st = fail(&S->shell, BDECON_ERR_CUDA, "launch table upload failed");
+        }
+        if (st == BDECON_OK) st = run_segment(ls, len, S->st, &S->shell, nullptr, lens.data());
         if (st == BDECON_OK) st = check_device(&S->shell);
         if (st != BDECON_OK) {
             const std::string m = S->shell.err;
@@ -1638,8 +1676,9 @@ void srv_loop(bdecon_server* S)
             ++S->segments;
         }
         std::vector<SrvJob*> keep;
-        for (SrvJob* j : S->active) {
-            j->remaining -= len;
+        for (size_t hi = 0; hi < S->active.size(); ++hi) {
+            SrvJob* j = S->active[hi];
+            j->remaining -= lens[hi];
             if (j->remaining > 0) {
                 keep.push_back(j);
                 continue;

@@ -131,3 +131,24 @@ def test_stop_with_queued_jobs_frees_everything():
     srv.close()                      # returns: the running segment completes, every job ends failed or done
     free1, _ = torch.cuda.mem_get_info()
     assert free1 >= free0 - (64 << 20)
+
+
+def test_light_job_takes_more_sweeps_per_segment_and_finishes_first():
+    # a 320x320 job with 4 chains has more patches than the GPU holds blocks,
+    # so its blocks take several patches in turn; a small job in the same
+    # launch group takes proportionally more sweeps per segment and is done
+    # long before the large one, with a result still identical to running alone
+    big = synth.small_problem(H=320, W=320, L=9, seed=201)
+    big.n_chains = 4
+    small = synth.small_problem(H=24, W=24, L=9, seed=202)
+    srv = bdecon.Server(mem_budget=8 << 30, max_jobs=4, segment_sweeps=4, precision=bdecon.BDECON_FP32)
+    try:
+        ib = srv.submit(big, 30)
+        i_s = srv.submit(small, 30)
+        ms, ts = srv.result(i_s, timeout=300)
+        mb, tb = srv.result(ib, timeout=300)
+    finally:
+        srv.close()
+    assert ts[2] < tb[2]
+    np.testing.assert_array_equal(ms, _alone(small, 30, bdecon.BDECON_FP32))
+    np.testing.assert_array_equal(mb, _alone(big, 30, bdecon.BDECON_FP32))
