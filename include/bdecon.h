@@ -98,6 +98,13 @@ typedef struct {
                                   PSF-window pixels).  It fixes the order of the
                                   per-update float reductions, so a problem gives
                                   the same chain alone or in any batch and plan.  */
+    int32_t sample_every;      /* keep the object after every this-many-th sweep past
+                                  burn_in (0 -> 1): the candidate images from which
+                                  quantiles and credible intervals are taken        */
+    int32_t n_samples;         /* kept objects per chain, >= 0 (0: none kept); the
+                                  sweep t > burn_in with (t - burn_in) a multiple of
+                                  sample_every goes to slot (t - burn_in) /
+                                  sample_every - 1 while that is < n_samples        */
 } bdecon_problem;
 
 #define BDECON_FLAG_ACCEPT_LOG 1   /* keep the accept decision of every update of
@@ -159,6 +166,29 @@ bdecon_status bdecon_posterior_mean(bdecon_handle* h, int32_t p, double* out, in
 /* Per-pixel posterior variance (needs BDECON_FLAG_SECOND_MOMENT), same
  * layout and pooling as bdecon_posterior_mean.                             */
 bdecon_status bdecon_posterior_var(bdecon_handle* h, int32_t p, double* out, int32_t crop);
+
+/* Uncertainty maps pooled over the chains of problem p, laid out as
+ * bdecon_posterior_mean (both need BDECON_FLAG_SECOND_MOMENT): the posterior
+ * standard deviation sqrt(var), and the coefficient of variation std / mean
+ * (the paper's relative uncertainty map).                                  */
+bdecon_status bdecon_posterior_std(bdecon_handle* h, int32_t p, double* out, int32_t crop);
+bdecon_status bdecon_posterior_cv(bdecon_handle* h, int32_t p, double* out, int32_t crop);
+
+/* The kept objects of chain c of problem p (see n_samples), oldest first,
+ * each (H+2R)*(W+2R) doubles, into host out (capacity cap doubles); *n
+ * receives the doubles available (kept objects x object pixels).          */
+bdecon_status bdecon_get_samples(bdecon_handle* h, int32_t p, int32_t c, double* out, size_t cap,
+                                 size_t* n);
+
+/* Per-pixel quantiles of the kept objects of all chains of problem p, for
+ * each of nq (1..64) probabilities q[k] in [0, 1]: with the n kept values of
+ * a pixel sorted, x_(0) <= ... <= x_(n-1), the value at h = (n - 1) q is
+ * x_(floor h) + (h - floor h)(x_(floor h + 1) - x_(floor h)) (linear
+ * interpolation between order statistics).  out: nq maps, each laid out as
+ * bdecon_posterior_mean.  Sorting runs on the device; at most 8192 kept
+ * values per pixel (kept objects x chains).                                */
+bdecon_status bdecon_posterior_quantiles(bdecon_handle* h, int32_t p, const double* q, int32_t nq,
+                                         double* out, int32_t crop);
 
 /* Log posterior (Eq. 9 without the constant log B(alpha) terms) of chain c
  * of problem p after each sweep so far, into host out (capacity cap);

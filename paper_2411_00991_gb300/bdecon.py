@@ -45,7 +45,7 @@ class _Problem(C.Structure):
                 ("stride", C.c_int32), ("n_chains", C.c_int32), ("seed", C.c_uint64),
                 ("step", C.c_double), ("burn_in", C.c_int32), ("refresh_every", C.c_int32),
                 ("precision", C.c_int32), ("max_sweeps", C.c_int32), ("flags", C.c_int32),
-                ("team_warps", C.c_int32)]
+                ("team_warps", C.c_int32), ("sample_every", C.c_int32), ("n_samples", C.c_int32)]
 
 
 EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bdecon_create_in",
@@ -56,7 +56,8 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_get_plan", "bdecon_launch_count", "bdecon_set_timing", "bdecon_sweep_kernel_time",
            "bdecon_log_posterior_static", "bdecon_set_fault", "bdecon_server_start",
            "bdecon_server_submit", "bdecon_server_poll", "bdecon_server_wait", "bdecon_server_stats",
-           "bdecon_server_stop", "bdecon_set_grouping", "bdecon_autotune", "bdecon_set_graph"]
+           "bdecon_server_stop", "bdecon_set_grouping", "bdecon_autotune", "bdecon_set_graph",
+           "bdecon_posterior_std", "bdecon_posterior_cv", "bdecon_get_samples", "bdecon_posterior_quantiles"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -87,6 +88,10 @@ def load(build_if_missing: bool = True):
         "bdecon_sync": [H],
         "bdecon_posterior_mean": [H, i32, vp, i32],
         "bdecon_posterior_var": [H, i32, vp, i32],
+        "bdecon_posterior_std": [H, i32, vp, i32],
+        "bdecon_posterior_cv": [H, i32, vp, i32],
+        "bdecon_get_samples": [H, i32, i32, vp, sz, C.POINTER(sz)],
+        "bdecon_posterior_quantiles": [H, i32, vp, i32, vp, i32],
         "bdecon_log_posterior_trace": [H, i32, i32, vp, sz, C.POINTER(sz)],
         "bdecon_accept_counts": [H, i32, i32, vp, sz, C.POINTER(sz)],
         "bdecon_accept_log": [H, i32, i32, vp, sz, C.POINTER(sz)],
@@ -153,7 +158,8 @@ def _problem(pr, precision, max_sweeps, flags, keep) -> _Problem:
     return _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
                     int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
                     int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
-                    int(flags), int(getattr(pr, "team_warps", 0)))
+                    int(flags), int(getattr(pr, "team_warps", 0)), int(getattr(pr, "sample_every", 0)),
+                    int(getattr(pr, "n_samples", 0)))
 
 
 def log_posterior_static(H, W, image_ptr, L, psf_ptr, gain, offset, var, stride, rho_ptr, out_ptr,
@@ -263,6 +269,36 @@ class Sampler:
         H, W, Ho, Wo = self._shape(p)
         out = np.empty((H, W) if crop else (Ho, Wo))
         self._ck(self.L.bdecon_posterior_var(self.h, p, _p(out), int(crop)))
+        return out
+
+    def posterior_std(self, p: int = 0, crop: bool = False) -> np.ndarray:
+        H, W, Ho, Wo = self._shape(p)
+        out = np.empty((H, W) if crop else (Ho, Wo))
+        self._ck(self.L.bdecon_posterior_std(self.h, p, _p(out), int(crop)))
+        return out
+
+    def posterior_cv(self, p: int = 0, crop: bool = False) -> np.ndarray:
+        """Coefficient of variation std / mean (relative uncertainty)."""
+        H, W, Ho, Wo = self._shape(p)
+        out = np.empty((H, W) if crop else (Ho, Wo))
+        self._ck(self.L.bdecon_posterior_cv(self.h, p, _p(out), int(crop)))
+        return out
+
+    def samples(self, p: int = 0, c: int = 0) -> np.ndarray:
+        """Kept objects of chain c, (k, H+2R, W+2R), oldest first."""
+        H, W, Ho, Wo = self._shape(p)
+        n = C.c_size_t()
+        self._ck(self.L.bdecon_get_samples(self.h, p, c, None, 0, C.byref(n)))
+        out = np.empty(n.value)
+        self._ck(self.L.bdecon_get_samples(self.h, p, c, _p(out), out.size, C.byref(n)))
+        return out.reshape(-1, Ho, Wo)
+
+    def posterior_quantiles(self, q, p: int = 0, crop: bool = False) -> np.ndarray:
+        """Per-pixel quantiles of the kept objects of all chains, (len(q), ...)."""
+        H, W, Ho, Wo = self._shape(p)
+        qa = np.ascontiguousarray(np.atleast_1d(np.asarray(q, dtype=np.float64)))
+        out = np.empty((qa.size, H, W) if crop else (qa.size, Ho, Wo))
+        self._ck(self.L.bdecon_posterior_quantiles(self.h, p, _p(qa), qa.size, _p(out), int(crop)))
         return out
 
     def trace(self, p: int = 0, c: int = 0) -> np.ndarray:

@@ -53,6 +53,7 @@ struct Image {
     int64_t spec_len;                // complex elements per chain
     int n_ent, n_tw, max_nhalf;      // table sizes (all shapes)
     int team;                        // threads per pixel update (a property of the problem)
+    int sample_every, n_samples;     // kept objects: every sample_every-th sweep past burn-in, n_samples slots
 };
 
 // One chain (an instance of a problem with its own state and random stream).
@@ -75,6 +76,7 @@ struct Chain {
     int cta_base;                    // first block of this chain in the sweep grid
     int* tdev;                       // sweeps this chain has completed (device counter, advanced by k_trace)
     int n_sweeps;                    // sweeps of this chain in the launch (0: the launch's n_sweeps)
+    void* samples;                   // [n_samples][Ho*Wo] T kept objects, or null
 };
 
 struct SweepArgs {
@@ -175,8 +177,20 @@ void launch_set_rho(const double* src, void* dst, int64_t n, cudaStream_t st, in
 void launch_set_counters(const Chain* d_chains, int n_chains, int value, cudaStream_t st, int64_t* launches);
 // sets the thread-local message that bdecon_last_error(NULL) returns
 void set_host_error(const char* msg);
+// pooled map of the chains' running sums: kind 0 mean, 1 variance, 2 standard
+// deviation, 3 coefficient of variation (1-3 need the sums of squares sq)
 void launch_mean(const double* sum, int n_chains_img, int64_t chain_stride_elems, int Ho, int Wo,
                  int crop_r, int out_h, int out_w, double inv_n, double* out, const double* sq,
-                 int want_var, cudaStream_t st, int64_t* launches);
+                 int kind, cudaStream_t st, int64_t* launches);
+constexpr int kMaxQuantiles = 64;
+constexpr int kMaxQuantileValues = 8192;
+// quantiles q[0..nq) of the kept objects (slots [first, first + count) of
+// every chain; chain c's store at samples + c * chain_stride elements) for
+// the object pixels pix0 .. pix0 + npix - 1 of the (cropped) output grid;
+// out[k * npix + i] for quantile k of pixel pix0 + i
+template <typename T>
+cudaError_t launch_quantiles(const void* samples, int64_t chain_stride, int n_chains, int first, int count,
+                             int64_t obj_pixels, int Wo, int crop_r, int out_w, int64_t pix0, int64_t npix,
+                             const double* q, int nq, double* out, cudaStream_t st, int64_t* launches);
 
 }  // namespace bd

@@ -410,9 +410,10 @@ void launch_set_rho(const double* src, void* dst, int64_t n, cudaStream_t st, in
 template void launch_set_rho<float>(const double*, void*, int64_t, cudaStream_t, int64_t*);
 template void launch_set_rho<double>(const double*, void*, int64_t, cudaStream_t, int64_t*);
 
-// posterior mean (and variance) pooled over the chains of one problem
+// posterior mean (variance, standard deviation, coefficient of variation)
+// pooled over the chains of one problem
 __global__ void k_mean(const double* sum, int n_chains, int64_t stride, int Wo, int crop_r, int oh, int ow,
-                       double inv_n, double* out, const double* sq, int want_var)
+                       double inv_n, double* out, const double* sq, int kind)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= oh * ow) return;
@@ -421,21 +422,97 @@ __global__ void k_mean(const double* sum, int n_chains, int64_t stride, int Wo, 
     double s = 0.0, q = 0.0;
     for (int c = 0; c < n_chains; ++c) {
         s += sum[c * stride + m];
-        if (want_var) q += sq[c * stride + m];
+        if (kind) q += sq[c * stride + m];
     }
     const double mean = s * inv_n;
-    out[idx] = want_var ? fmax(q * inv_n - mean * mean, 0.0) : mean;
+    if (kind == 0) {
+        out[idx] = mean;
+        return;
+    }
+    const double var = fmax(q * inv_n - mean * mean, 0.0);
+    out[idx] = kind == 1 ? var : kind == 2 ? sqrt(var) : sqrt(var) / mean;
 }
 
 void launch_mean(const double* sum, int n_chains_img, int64_t chain_stride_elems, int Ho, int Wo, int crop_r,
-                 int out_h, int out_w, double inv_n, double* out, const double* sq, int want_var, cudaStream_t st,
+                 int out_h, int out_w, double inv_n, double* out, const double* sq, int kind, cudaStream_t st,
                  int64_t* launches)
 {
     (void)Ho;
     const int n = out_h * out_w;
     k_mean<<<(n + 255) / 256, 256, 0, st>>>(sum, n_chains_img, chain_stride_elems, Wo, crop_r, out_h, out_w, inv_n,
-                                            out, sq, want_var);
+                                            out, sq, kind);
     ++*launches;
 }
+
+// ------------------------------------------------------------ quantiles --
+// One block per output pixel: the pixel's kept values of every chain are
+// loaded into shared memory, padded with +inf to a power of two, sorted by a
+// bitonic network, and each requested quantile is read off the order
+// statistics by linear interpolation at h = (n - 1) q.
+template <typename T>
+__global__ void __launch_bounds__(256) k_quantiles(const T* samples, int64_t chain_stride, int n_chains, int first,
+                                                  int count, int64_t obj_pixels, int Wo, int crop_r, int out_w,
+                                                  int64_t pix0, int npow2, const double* q, int nq, double* out,
+                                                  int64_t npix)
+{
+    extern __shared__ double sv[];
+    const int64_t i = blockIdx.x;
+    const int64_t pix = pix0 + i;
+    const int64_t y = pix / out_w + crop_r, x = pix % out_w + crop_r;
+    const int64_t m = y * Wo + x;
+    const int n = count * n_chains;
+    for (int k = threadIdx.x; k < npow2; k += blockDim.x) {
+        double v = INFINITY;
+        if (k < n) {
+            const int c = k / count, slot = first + (k - c * count);
+            v = (double)samples[c * chain_stride + (int64_t)slot * obj_pixels + m];
+        }
+        sv[k] = v;
+    }
+    __syncthreads();
+    for (int size = 2; size <= npow2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int k = threadIdx.x; k < npow2 / 2; k += blockDim.x) {
+                // element pair (a, b) of this stage, ascending where (a & size) == 0
+                const int a = 2 * k - (k & (stride - 1)), b = a + stride;
+                const bool up = (a & size) == 0;
+                const double va = sv[a], vb = sv[b];
+                if ((va > vb) == up) {
+                    sv[a] = vb;
+                    sv[b] = va;
+                }
+            }
+            __syncthreads();
+        }
+    for (int k = threadIdx.x; k < nq; k += blockDim.x) {
+        const double h = (double)(n - 1) * q[k];
+        int lo = (int)floor(h);
+        lo = lo < 0 ? 0 : lo > n - 1 ? n - 1 : lo;
+        const int hi = lo + 1 < n ? lo + 1 : n - 1;
+        out[(int64_t)k * npix + i] = sv[lo] + (h - (double)lo) * (sv[hi] - sv[lo]);
+    }
+}
+
+template <typename T>
+cudaError_t launch_quantiles(const void* samples, int64_t chain_stride, int n_chains, int first, int count,
+                             int64_t obj_pixels, int Wo, int crop_r, int out_w, int64_t pix0, int64_t npix,
+                             const double* q, int nq, double* out, cudaStream_t st, int64_t* launches)
+{
+    int npow2 = 2;
+    while (npow2 < count * n_chains) npow2 <<= 1;
+    const size_t smem = sizeof(double) * (size_t)npow2;
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_quantiles<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_quantiles<T><<<(unsigned)npix, 256, smem, st>>>(reinterpret_cast<const T*>(samples), chain_stride, n_chains,
+                                                      first, count, obj_pixels, Wo, crop_r, out_w, pix0, npow2, q,
+                                                      nq, out, npix);
+    ++*launches;
+    return cudaGetLastError();
+}
+template cudaError_t launch_quantiles<float>(const void*, int64_t, int, int, int, int64_t, int, int, int, int64_t,
+                                             int64_t, const double*, int, double*, cudaStream_t, int64_t*);
+template cudaError_t launch_quantiles<double>(const void*, int64_t, int, int, int, int64_t, int, int, int, int64_t,
+                                              int64_t, const double*, int, double*, cudaStream_t, int64_t*);
 
 }  // namespace bd

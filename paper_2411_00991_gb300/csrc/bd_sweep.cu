@@ -444,17 +444,25 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             __syncthreads();
         }
         if (c == S2 - 1) {
-            // a7: after the sweep, add the object to the running sums (own patches only)
+            // a7: after the sweep, add the object to the running sums (own
+            // patches only) and, every sample_every-th sweep, keep it
             if (t > im.burn_in) {
+                const int ks = t - im.burn_in;
+                const int slot_k = (ch.samples != nullptr && ks % im.sample_every == 0) ? ks / im.sample_every - 1 : -1;
+                T* keep = slot_k >= 0 && slot_k < im.n_samples
+                              ? reinterpret_cast<T*>(ch.samples) + (size_t)slot_k * im.Ho * im.Wo
+                              : nullptr;
                 for (int q = 0; q < npt; ++q) {
                     const int pi = pi0 + q / tw_, pj = pj0 + (q - (q / tw_) * tw_);
                     const Shape& sh = im.shape[shape_index(im, pi, pj)];
                     for (int e = tid; e < sh.ph * sh.pw; e += blockDim.x) {
                         const int uu = e / sh.pw, vv = e - (e / sh.pw) * sh.pw;
                         const size_t mm = (size_t)(pi * S + uu) * im.Wo + pj * S + vv;
-                        const double rv = RES ? (double)rho_s[(size_t)q * S2 + uu * S + vv] : (double)rho_g[mm];
+                        const T r = RES ? rho_s[(size_t)q * S2 + uu * S + vv] : rho_g[mm];
+                        const double rv = (double)r;
                         ch.rho_sum[mm] += rv;
                         if (ch.rho_sq) ch.rho_sq[mm] += rv * rv;
+                        if (keep) keep[mm] = r;
                     }
                 }
             }

@@ -44,7 +44,8 @@ struct ProbHost {
     int max_nhalf = 0;
     // arena offsets (bytes)
     size_t o_K64, o_K32, o_dat64, o_dat32, o_ekl, o_wa64, o_m64, o_wa32, o_m32, o_tw64, o_tw32, o_poff;
-    size_t o_sum, o_sq, o_scr;
+    size_t o_sum, o_sq, o_scr, o_samp;
+    int samp_first = 0;         // first valid kept-object slot (after a resume)
     size_t scr_doubles;
     int chain0;
 };
@@ -161,6 +162,9 @@ bdecon_status validate(const bdecon_problem& p, int idx)
         return fail(nullptr, BDECON_ERR_INVALID, "problem %d: stride %d must be in [L=%d, %d]", idx, S, p.L, kMaxS);
     if (p.n_chains < 1 || p.n_chains > 4096) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: n_chains %d", idx, p.n_chains);
     if (p.team_warps < 0 || p.team_warps > 8) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: team_warps %d", idx, p.team_warps);
+    if (p.n_samples < 0 || p.sample_every < 0)
+        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: n_samples %d / sample_every %d must be >= 0", idx, p.n_samples,
+                    p.sample_every);
     if (p.precision != BDECON_FP32 && p.precision != BDECON_FP64)
         return fail(nullptr, BDECON_ERR_INVALID, "problem %d: precision %d", idx, p.precision);
     if (p.burn_in < 0 || p.refresh_every < 0 || p.max_sweeps < 0)
@@ -448,6 +452,7 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
         ph.o_poff = A.take(8 * ph.n_patches);
         ph.o_sum = A.take(8 * nobj * ph.p.n_chains);
         ph.o_sq = (ph.p.flags & BDECON_FLAG_SECOND_MOMENT) ? A.take(8 * nobj * ph.p.n_chains) : 0;
+        ph.o_samp = ph.p.n_samples > 0 ? A.take(ts * nobj * (size_t)ph.p.n_samples * ph.p.n_chains) : 0;
         const size_t nblk = (npix + kRedThreads - 1) / kRedThreads;
         ph.scr_doubles = std::max(nblk + (size_t)ph.n_patches + 8, nblk + 8 + 2 * (size_t)kMaxS * kMaxS) + 8;
         ph.o_scr = A.take(8 * ph.scr_doubles);
@@ -594,6 +599,8 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         im.team = problem_team(ph.L, ph.p.n_chains, ph.n_patches, ph.p.team_warps);
         im.n_tw = ph.n_tw;
         im.max_nhalf = ph.max_nhalf;
+        im.sample_every = ph.p.sample_every > 0 ? ph.p.sample_every : 1;
+        im.n_samples = ph.p.n_samples;
     }
     h->chains.resize(h->chh.size());
     for (int k = 0; k < n; ++k) {
@@ -617,6 +624,8 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
             ch.acc_step = (int*)(A + x.o_astep);
             ch.trace = (double*)(A + x.o_trace);
             ch.tdev = (int*)(A + x.o_tdev);
+            ch.samples = ph.o_samp ? A + ph.o_samp + (h->precision == BDECON_FP32 ? 4 : 8) * nobj * ph.p.n_samples * c
+                                   : nullptr;
         }
     }
     if (cudaMemcpyAsync(h->d_imgs, h->imgs.data(), sizeof(Image) * n, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
@@ -996,19 +1005,116 @@ bdecon_status bdecon_posterior_mean(bdecon_handle* h, int32_t p, double* out, in
     return check_device(h);
 }
 
-bdecon_status bdecon_posterior_var(bdecon_handle* h, int32_t p, double* out, int32_t crop)
+namespace {
+
+// Pooled map of kind 0..3 (mean, variance, std, cv) into host out.
+bdecon_status pooled_map(bdecon_handle* h, int32_t p, double* out, int32_t crop, int kind)
 {
     if (!h || !out) return fail(h, BDECON_ERR_INVALID, "bad arguments");
     int ci;
     bdecon_status s = chain_index(h, p, 0, &ci);
     if (s != BDECON_OK) return s;
     ProbHost& ph = h->probs[p];
-    if (!ph.o_sq) return fail(h, BDECON_ERR_STATE, "created without BDECON_FLAG_SECOND_MOMENT");
+    if (kind > 0 && !ph.o_sq) return fail(h, BDECON_ERR_STATE, "created without BDECON_FLAG_SECOND_MOMENT");
     if (ph.n_sum == 0) return fail(h, BDECON_ERR_STATE, "no sweep after burn-in yet");
     const int oh = crop ? ph.H : ph.Ho, ow = crop ? ph.W : ph.Wo;
     launch_mean(h->chains[ci].rho_sum, ph.p.n_chains, (int64_t)ph.Ho * ph.Wo, ph.Ho, ph.Wo, crop ? ph.R : 0, oh, ow,
-                1.0 / ((double)ph.n_sum * ph.p.n_chains), h->d_up, h->chains[ci].rho_sq, 1, h->st, &h->launches);
+                1.0 / ((double)ph.n_sum * ph.p.n_chains), h->d_up, h->chains[ci].rho_sq, kind, h->st, &h->launches);
     CK(h, cudaMemcpyAsync(out, h->d_up, 8 * (size_t)oh * ow, cudaMemcpyDeviceToHost, h->st));
+    return check_device(h);
+}
+
+// Kept-object slots of problem p filled so far: [first, first + count).
+void kept_range(const bdecon_handle* h, const ProbHost& ph, int& first, int& count)
+{
+    const int every = ph.p.sample_every > 0 ? ph.p.sample_every : 1;
+    const int64_t past = h->sweeps - ph.p.burn_in;
+    const int64_t filled = past > 0 ? std::min<int64_t>(past / every, ph.p.n_samples) : 0;
+    first = (int)std::min<int64_t>(ph.samp_first, filled);
+    count = (int)filled - first;
+}
+
+}  // namespace
+
+bdecon_status bdecon_posterior_var(bdecon_handle* h, int32_t p, double* out, int32_t crop)
+{
+    return pooled_map(h, p, out, crop, 1);
+}
+
+bdecon_status bdecon_posterior_std(bdecon_handle* h, int32_t p, double* out, int32_t crop)
+{
+    return pooled_map(h, p, out, crop, 2);
+}
+
+bdecon_status bdecon_posterior_cv(bdecon_handle* h, int32_t p, double* out, int32_t crop)
+{
+    return pooled_map(h, p, out, crop, 3);
+}
+
+bdecon_status bdecon_get_samples(bdecon_handle* h, int32_t p, int32_t c, double* out, size_t cap, size_t* n)
+{
+    if (!h || !n) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    const ProbHost& ph = h->probs[p];
+    int first, count;
+    kept_range(h, ph, first, count);
+    const size_t nobj = (size_t)ph.Ho * ph.Wo;
+    *n = (size_t)count * nobj;
+    if (out && cap) {
+        const size_t ts = h->precision == BDECON_FP32 ? 4 : 8;
+        for (int k = 0; k < count && (size_t)(k + 1) * nobj <= cap; ++k) {
+            const char* src = (const char*)h->chains[ci].samples + ts * nobj * (size_t)(first + k);
+            if (h->precision == BDECON_FP32) launch_convert<float>(src, h->d_up, (int64_t)nobj, ph.Ho, ph.Wo, ph.Wo, h->st, &h->launches);
+            else launch_convert<double>(src, h->d_up, (int64_t)nobj, ph.Ho, ph.Wo, ph.Wo, h->st, &h->launches);
+            CK(h, cudaMemcpyAsync(out + (size_t)k * nobj, h->d_up, 8 * nobj, cudaMemcpyDeviceToHost, h->st));
+        }
+    }
+    return check_device(h);
+}
+
+bdecon_status bdecon_posterior_quantiles(bdecon_handle* h, int32_t p, const double* q, int32_t nq, double* out,
+                                         int32_t crop)
+{
+    if (!h || !q || !out) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    if (nq < 1 || nq > kMaxQuantiles) return fail(h, BDECON_ERR_INVALID, "nq must be 1..%d", kMaxQuantiles);
+    for (int k = 0; k < nq; ++k)
+        if (!(q[k] >= 0.0 && q[k] <= 1.0)) return fail(h, BDECON_ERR_INVALID, "q[%d] must be in [0, 1]", k);
+    int ci;
+    bdecon_status s = chain_index(h, p, 0, &ci);
+    if (s != BDECON_OK) return s;
+    const ProbHost& ph = h->probs[p];
+    if (!ph.o_samp) return fail(h, BDECON_ERR_STATE, "created with n_samples = 0");
+    int first, count;
+    kept_range(h, ph, first, count);
+    if (count < 1) return fail(h, BDECON_ERR_STATE, "no object kept yet");
+    if ((int64_t)count * ph.p.n_chains > kMaxQuantileValues)
+        return fail(h, BDECON_ERR_INVALID, "%d kept values per pixel, at most %d", count * ph.p.n_chains, kMaxQuantileValues);
+    s = check_device(h);
+    if (s != BDECON_OK) return s;
+    const int oh = crop ? ph.H : ph.Ho, ow = crop ? ph.W : ph.Wo;
+    const int64_t npix = (int64_t)oh * ow, nobj = (int64_t)ph.Ho * ph.Wo;
+    // staging in d_up: the probabilities, then nq values per pixel of a chunk
+    double* dq = h->d_up;
+    double* dout = h->d_up + kMaxQuantiles;
+    const int64_t chunk = ((int64_t)(h->up_bytes / 8) - kMaxQuantiles) / nq;
+    if (chunk < 1) return fail(h, BDECON_ERR_NOMEM, "staging buffer too small");
+    CK(h, cudaMemcpyAsync(dq, q, 8 * (size_t)nq, cudaMemcpyHostToDevice, h->st));
+    const int64_t cstride = nobj * ph.p.n_samples;
+    for (int64_t p0 = 0; p0 < npix; p0 += chunk) {
+        const int64_t np = std::min(chunk, npix - p0);
+        cudaError_t e = h->precision == BDECON_FP32
+                            ? launch_quantiles<float>(h->chains[ci].samples, cstride, ph.p.n_chains, first, count, nobj,
+                                                      ph.Wo, crop ? ph.R : 0, ow, p0, np, dq, nq, dout, h->st, &h->launches)
+                            : launch_quantiles<double>(h->chains[ci].samples, cstride, ph.p.n_chains, first, count, nobj,
+                                                       ph.Wo, crop ? ph.R : 0, ow, p0, np, dq, nq, dout, h->st, &h->launches);
+        if (e != cudaSuccess) return fail(h, BDECON_ERR_CUDA, "quantile kernel: %s", cudaGetErrorString(e));
+        for (int k = 0; k < nq; ++k)
+            CK(h, cudaMemcpyAsync(out + (size_t)k * npix + p0, dout + (size_t)k * np, 8 * (size_t)np,
+                                  cudaMemcpyDeviceToHost, h->st));
+        CK(h, cudaStreamSynchronize(h->st));   // the staging buffer is reused by the next chunk
+    }
     return check_device(h);
 }
 
@@ -1109,6 +1215,11 @@ bdecon_status bdecon_set_state(bdecon_handle* h, int32_t p, int32_t c, const dou
     }
     for (auto& ph : h->probs) {
         ph.n_sum = 0;
+        {   // objects kept before the resume point are not this run's
+            const int every = ph.p.sample_every > 0 ? ph.p.sample_every : 1;
+            const int64_t past = sweeps - ph.p.burn_in;
+            ph.samp_first = past > 0 ? (int)std::min<int64_t>(past / every, ph.p.n_samples) : 0;
+        }
         for (int k = 0; k < ph.p.n_chains; ++k) {
             const Chain& ch = h->chains[ph.chain0 + k];
             CK(h, cudaMemsetAsync(ch.rho_sum, 0, 8 * (size_t)ph.Ho * ph.Wo, h->st));

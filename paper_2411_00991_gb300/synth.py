@@ -46,6 +46,8 @@ class Problem:
     truth: Optional[np.ndarray] = None
     name: str = ""
     team_warps: int = 0          # 0 -> chosen by the library from the problem alone
+    sample_every: int = 0        # keep every k-th post-burn-in object (0 -> 1)
+    n_samples: int = 0           # kept objects per chain (0 -> none)
 
     @property
     def H(self) -> int:

@@ -34,7 +34,7 @@ def _problem_struct(prob, **over):
     psf = np.ascontiguousarray(prob.psf, dtype=np.float64)
     keep = [img, psf]
     p = bdecon._Problem(prob.H, prob.W, img.ctypes.data, prob.L, psf.ctypes.data, None, 2.0, None, 100.0,
-                        None, 2.56, 0, 1, 0, 0.2, 0, 10, bdecon.BDECON_FP32, 64, 0, 0)
+                        None, 2.56, 0, 1, 0, 0.2, 0, 10, bdecon.BDECON_FP32, 64, 0, 0, 0, 0)
     for k, v in over.items():
         setattr(p, k, v)
     return p, keep
@@ -52,6 +52,7 @@ def _problem_struct(prob, **over):
     ("step", float("nan"), "step"),
     ("refresh_every", -1, "negative"),
     ("team_warps", 9, "team_warps"),
+    ("n_samples", -1, "n_samples"),
 ])
 def test_invalid_problem_refused(field, value, msg):
     L = bdecon.load()
@@ -89,6 +90,14 @@ def test_null_handle_calls_are_refused():
     n = C.c_int64()
     assert L.bdecon_launch_count(None, C.byref(n)) == 1
     L.bdecon_destroy(None)
+
+
+def test_workspace_size_grows_with_kept_objects():
+    prob = synth.small_problem(H=30, W=31, L=5)
+    a = bdecon.Sampler.workspace_size(prob)
+    prob.n_samples = 10
+    b = bdecon.Sampler.workspace_size(prob)
+    assert b - a >= 10 * (30 + 4) * (31 + 4) * 4
 
 
 def test_workspace_size_grows_with_chains():
