@@ -105,6 +105,12 @@ typedef struct {
                                   sweep t > burn_in with (t - burn_in) a multiple of
                                   sample_every goes to slot (t - burn_in) /
                                   sample_every - 1 while that is < n_samples        */
+    double adapt_target;       /* 0: every pixel proposes with `step`.  In (0, 1):
+                                  during burn-in each pixel m adapts its own scale
+                                  s_m (from `step`): after its update in sweep t,
+                                  s_m *= exp(g (1 - adapt_target)) if accepted,
+                                  exp(-g adapt_target) if not, g = 0.5/sqrt(t),
+                                  clamped to [1e-4, 4]; fixed after burn-in      */
 } bdecon_problem;
 
 #define BDECON_FLAG_ACCEPT_LOG 1   /* keep the accept decision of every update of
@@ -173,6 +179,10 @@ bdecon_status bdecon_posterior_var(bdecon_handle* h, int32_t p, double* out, int
  * (the paper's relative uncertainty map).                                  */
 bdecon_status bdecon_posterior_std(bdecon_handle* h, int32_t p, double* out, int32_t crop);
 bdecon_status bdecon_posterior_cv(bdecon_handle* h, int32_t p, double* out, int32_t crop);
+
+/* Per-pixel proposal scales of chain c of problem p, (H+2R)*(W+2R)
+ * doubles: the adapted s_m (see adapt_target), else `step` everywhere.   */
+bdecon_status bdecon_get_steps(bdecon_handle* h, int32_t p, int32_t c, double* out);
 
 /* The kept objects of chain c of problem p (see n_samples), oldest first,
  * each (H+2R)*(W+2R) doubles, into host out (capacity cap doubles); *n

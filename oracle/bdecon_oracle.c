@@ -25,6 +25,14 @@
  * single-site Metropolis-Hastings step per object pixel per sweep,
  * systematic scan over sub-lattice classes, log-space Gaussian random walk
  * proposals keyed by Philox4x32-10 on (pixel, sweep, chain).
+ * Optional burn-in adaptation of the proposal scale (not in the paper, which
+ * leaves the proposal unstated): each pixel m has its own scale s_m, starting
+ * at step; during burn-in sweeps only, after each update of m,
+ * s_m <- s_m * exp(g_t (1 - a*)) if accepted, s_m * exp(-g_t a*) if not,
+ * clamped to [1e-4, 4], with a* the problem's target acceptance rate and the
+ * gain g_t = 0.5 / sqrt(t) of sweep t shrinking over burn-in, so that log s_m
+ * settles where the pixel's acceptance rate is a*; after burn-in the scales
+ * stay fixed and the chain is an ordinary Metropolis-Hastings chain.
  */
 #include <math.h>
 #include <stdint.h>
@@ -52,7 +60,13 @@ typedef struct {
     double step;         /* sd of the log-space random walk                    */
     int burn_in;         /* sweeps t <= burn_in are not averaged               */
     int refresh_every;   /* recompute mu and spectra every this many sweeps    */
+    double adapt_target; /* > 0: adapt the per-pixel proposal scale during
+                            burn-in toward this acceptance rate               */
 } or_problem;
+
+#define OR_ADAPT_GAIN 0.5
+#define OR_STEP_MIN 1e-4
+#define OR_STEP_MAX 4.0
 
 /* ------------------------------------------------------------------ RNG --
  * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
@@ -311,6 +325,7 @@ typedef struct {
     double** alpha;   /* per patch hyperparameter                         */
     double* tre;      /* scratch ph*pw                                    */
     double* tim;
+    double* steps;    /* per-pixel proposal scale, Ho*Wo                  */
 } chain_state;
 
 static void cs_refresh(chain_state* c)
@@ -356,6 +371,8 @@ static void cs_open(chain_state* c, const or_problem* P, const double* rho_in)
         }
     c->tre = (double*)malloc((size_t)c->S * c->S * sizeof(double));
     c->tim = (double*)malloc((size_t)c->S * c->S * sizeof(double));
+    c->steps = (double*)malloc((size_t)c->Ho * c->Wo * sizeof(double));
+    for (int m = 0; m < c->Ho * c->Wo; ++m) c->steps[m] = P->step;
     cs_refresh(c);
 }
 
@@ -364,7 +381,7 @@ static void cs_close(chain_state* c)
     int np = c->npi * c->npj;
     for (int p = 0; p < np; ++p) { free(c->sre[p]); free(c->sim[p]); free(c->alpha[p]); }
     free(c->sre); free(c->sim); free(c->alpha);
-    free(c->K); free(c->rho); free(c->mu); free(c->tre); free(c->tim);
+    free(c->K); free(c->rho); free(c->mu); free(c->tre); free(c->tim); free(c->steps);
 }
 
 /* Likelihood and prior changes for replacing rho_m (m = (i, j)) by rho_new
@@ -527,7 +544,8 @@ int or_single_update(const or_problem* P, const double* rho, int m, int t, int* 
  * and record the log posterior.                                             */
 int or_run(const or_problem* P, int t0, int T, int order, const double* rho_in,
            double* rho_out, double* mu_out, double* sum_out, int* n_sum,
-           double* trace, uint8_t* acc_log, double* samples, int64_t* n_acc)
+           double* trace, uint8_t* acc_log, double* samples, int64_t* n_acc,
+           double* steps_out)
 {
     chain_state c;
     cs_open(&c, P, rho_in);
@@ -537,6 +555,9 @@ int or_run(const or_problem* P, int t0, int T, int order, const double* rho_in,
     for (int tt = 1; tt <= T; ++tt) {
         const int t = t0 + tt;
         int64_t acc = 0;
+        /* this sweep's adaptation factors (burn-in sweeps only) */
+        const double gain = OR_ADAPT_GAIN / sqrt((double)t);
+        const double up = exp(gain * (1.0 - P->adapt_target)), down = exp(-gain * P->adapt_target);
         for (int u = 0; u < S; ++u)
             for (int v = 0; v < S; ++v) {
                 int ni = (Ho - 1 - u) / S + 1, nj = (Wo - 1 - v) / S + 1;
@@ -547,11 +568,16 @@ int or_run(const or_problem* P, int t0, int T, int order, const double* rho_in,
                         int i = u + ri * S, j = v + rj * S, m = i * Wo + j;
                         double z, uu;
                         or_draw(P->seed, (uint32_t)m, (uint32_t)t, (uint32_t)P->chain, &z, &uu);
-                        double rho_new = c.rho[m] * exp(P->step * z);
+                        const double sm = c.steps[m];
+                        double rho_new = c.rho[m] * exp(sm * z);
                         double dL, dP;
                         int ok = cs_delta(&c, i, j, rho_new, &dL, &dP);
-                        int accept = ok && (log(uu) < dL + dP + P->step * z);
+                        int accept = ok && (log(uu) < dL + dP + sm * z);
                         if (accept) { cs_accept(&c, i, j, rho_new); ++acc; }
+                        if (P->adapt_target > 0.0 && t <= P->burn_in) {
+                            double sn = sm * (accept ? up : down);
+                            c.steps[m] = sn < OR_STEP_MIN ? OR_STEP_MIN : sn > OR_STEP_MAX ? OR_STEP_MAX : sn;
+                        }
                         if (acc_log) acc_log[(size_t)(tt - 1) * Ho * Wo + m] = (uint8_t)accept;
                     }
             }
@@ -566,6 +592,7 @@ int or_run(const or_problem* P, int t0, int T, int order, const double* rho_in,
     }
     if (rho_out) memcpy(rho_out, c.rho, (size_t)Ho * Wo * sizeof(double));
     if (mu_out) memcpy(mu_out, c.mu, (size_t)P->H * P->W * sizeof(double));
+    if (steps_out) memcpy(steps_out, c.steps, (size_t)Ho * Wo * sizeof(double));
     if (n_sum) *n_sum = ns;
     cs_close(&c);
     return 0;

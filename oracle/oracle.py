@@ -39,7 +39,7 @@ class OrProblem(C.Structure):
                 ("w", C.c_void_p), ("gain", C.c_void_p), ("offset", C.c_void_p),
                 ("var", C.c_void_p), ("psf", C.c_void_p),
                 ("seed", C.c_uint64), ("chain", C.c_int), ("step", C.c_double),
-                ("burn_in", C.c_int), ("refresh_every", C.c_int)]
+                ("burn_in", C.c_int), ("refresh_every", C.c_int), ("adapt_target", C.c_double)]
 
 
 def lib():
@@ -66,7 +66,7 @@ def lib():
         L.or_delta.restype = C.c_int
         L.or_run.argtypes = [C.POINTER(OrProblem), C.c_int, C.c_int, C.c_int, C.c_void_p,
                              C.c_void_p, C.c_void_p, C.c_void_p, ip, C.c_void_p, C.c_void_p,
-                             C.c_void_p, C.c_void_p]
+                             C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_run.restype = C.c_int
         L.or_single_update.argtypes = [C.POINTER(OrProblem), C.c_void_p, C.c_int, C.c_int, ip, dp, dp, dp]
         L.or_single_update.restype = C.c_int
@@ -153,7 +153,7 @@ class Oracle:
         self.psf = np.ascontiguousarray(prob.psf, dtype=np.float64)
         self.c = OrProblem(prob.H, prob.W, prob.L, prob.S, _p(self.w), _p(self.g), _p(self.o),
                            _p(self.v), _p(self.psf), int(prob.seed), int(chain), float(prob.step),
-                           int(prob.burn_in), int(prob.refresh_every))
+                           int(prob.burn_in), int(prob.refresh_every), float(getattr(prob, "adapt_target", 0.0)))
         self.Ho, self.Wo = prob.object_shape()
 
     def log_posterior(self, rho: np.ndarray) -> float:
@@ -189,14 +189,15 @@ class Oracle:
         n_acc = np.empty(T, dtype=np.int64)
         acc = np.empty((T, Ho, Wo), dtype=np.uint8) if want_acc_log else None
         smp = np.empty((T, Ho, Wo)) if want_samples else None
+        steps = np.empty((Ho, Wo))
         ns = C.c_int()
         rin = None if rho_in is None else np.ascontiguousarray(rho_in, dtype=np.float64)
         lib().or_run(C.byref(self.c), int(t0), int(T), int(order), _p(rin), _p(rho_out), _p(mu_out),
-                     _p(sum_out), C.byref(ns), _p(trace), _p(acc), _p(smp), _p(n_acc))
+                     _p(sum_out), C.byref(ns), _p(trace), _p(acc), _p(smp), _p(n_acc), _p(steps))
         n = ns.value
         return dict(rho=rho_out, mu=mu_out, sum=sum_out, n_sum=n,
                     mean=(sum_out / n if n > 0 else None), trace=trace, acc_log=acc,
-                    samples=smp, n_acc=n_acc)
+                    samples=smp, n_acc=n_acc, steps=steps)
 
 
 if __name__ == "__main__":

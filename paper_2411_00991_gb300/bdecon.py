@@ -45,7 +45,8 @@ class _Problem(C.Structure):
                 ("stride", C.c_int32), ("n_chains", C.c_int32), ("seed", C.c_uint64),
                 ("step", C.c_double), ("burn_in", C.c_int32), ("refresh_every", C.c_int32),
                 ("precision", C.c_int32), ("max_sweeps", C.c_int32), ("flags", C.c_int32),
-                ("team_warps", C.c_int32), ("sample_every", C.c_int32), ("n_samples", C.c_int32)]
+                ("team_warps", C.c_int32), ("sample_every", C.c_int32), ("n_samples", C.c_int32),
+                ("adapt_target", C.c_double)]
 
 
 EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bdecon_create_in",
@@ -57,7 +58,8 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_log_posterior_static", "bdecon_set_fault", "bdecon_server_start",
            "bdecon_server_submit", "bdecon_server_poll", "bdecon_server_wait", "bdecon_server_stats",
            "bdecon_server_stop", "bdecon_set_grouping", "bdecon_autotune", "bdecon_set_graph",
-           "bdecon_posterior_std", "bdecon_posterior_cv", "bdecon_get_samples", "bdecon_posterior_quantiles"]
+           "bdecon_posterior_std", "bdecon_posterior_cv", "bdecon_get_samples", "bdecon_posterior_quantiles",
+           "bdecon_get_steps"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -98,6 +100,7 @@ def load(build_if_missing: bool = True):
         "bdecon_get_state": [H, i32, i32, vp, C.POINTER(i64)],
         "bdecon_set_state": [H, i32, i32, vp, i64],
         "bdecon_get_mu": [H, i32, i32, vp],
+        "bdecon_get_steps": [H, i32, i32, vp],
         "bdecon_log_posterior": [H, i32, i32, dp],
         "bdecon_delta": [H, i32, i32, i64, C.c_double, dp, dp, C.POINTER(i32)],
         "bdecon_set_plan": [H, i32, i32, i32, i32],
@@ -159,7 +162,7 @@ def _problem(pr, precision, max_sweeps, flags, keep) -> _Problem:
                     int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
                     int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
                     int(flags), int(getattr(pr, "team_warps", 0)), int(getattr(pr, "sample_every", 0)),
-                    int(getattr(pr, "n_samples", 0)))
+                    int(getattr(pr, "n_samples", 0)), float(getattr(pr, "adapt_target", 0.0)))
 
 
 def log_posterior_static(H, W, image_ptr, L, psf_ptr, gain, offset, var, stride, rho_ptr, out_ptr,
@@ -333,6 +336,13 @@ class Sampler:
     def set_state(self, rho: np.ndarray, sweeps: int, p: int = 0, c: int = 0):
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         self._ck(self.L.bdecon_set_state(self.h, p, c, _p(rho), int(sweeps)))
+
+    def get_steps(self, p: int = 0, c: int = 0) -> np.ndarray:
+        """Per-pixel proposal scales (adapted during burn-in when adapt_target > 0)."""
+        H, W, Ho, Wo = self._shape(p)
+        out = np.empty((Ho, Wo))
+        self._ck(self.L.bdecon_get_steps(self.h, p, c, _p(out)))
+        return out
 
     def get_mu(self, p: int = 0, c: int = 0) -> np.ndarray:
         H, W, Ho, Wo = self._shape(p)

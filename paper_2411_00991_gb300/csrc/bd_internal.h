@@ -54,6 +54,7 @@ struct Image {
     int n_ent, n_tw, max_nhalf;      // table sizes (all shapes)
     int team;                        // threads per pixel update (a property of the problem)
     int sample_every, n_samples;     // kept objects: every sample_every-th sweep past burn-in, n_samples slots
+    const double* adapt_fac;         // [burn_in][2] proposal-scale factors after accept / reject, or null
 };
 
 // One chain (an instance of a problem with its own state and random stream).
@@ -77,6 +78,7 @@ struct Chain {
     int* tdev;                       // sweeps this chain has completed (device counter, advanced by k_trace)
     int n_sweeps;                    // sweeps of this chain in the launch (0: the launch's n_sweeps)
     void* samples;                   // [n_samples][Ho*Wo] T kept objects, or null
+    void* steps;                     // [Ho*Wo] T per-pixel proposal scales (adapting problems), or null
 };
 
 struct SweepArgs {
@@ -173,6 +175,8 @@ void launch_convert(const void* src, double* dst, int64_t n, int rows, int cols,
                     cudaStream_t st, int64_t* launches);
 template <typename T>
 void launch_set_rho(const double* src, void* dst, int64_t n, cudaStream_t st, int64_t* launches);
+template <typename T>
+void launch_fill(void* dst, int64_t n, double value, cudaStream_t st, int64_t* launches);
 // sets every chain's sweep counter to value
 void launch_set_counters(const Chain* d_chains, int n_chains, int value, cudaStream_t st, int64_t* launches);
 // sets the thread-local message that bdecon_last_error(NULL) returns

@@ -410,6 +410,22 @@ void launch_set_rho(const double* src, void* dst, int64_t n, cudaStream_t st, in
 template void launch_set_rho<float>(const double*, void*, int64_t, cudaStream_t, int64_t*);
 template void launch_set_rho<double>(const double*, void*, int64_t, cudaStream_t, int64_t*);
 
+template <typename T>
+__global__ void k_fill(T* dst, int64_t n, T value)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) dst[idx] = value;
+}
+
+template <typename T>
+void launch_fill(void* dst, int64_t n, double value, cudaStream_t st, int64_t* launches)
+{
+    k_fill<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<T*>(dst), n, (T)value);
+    ++*launches;
+}
+template void launch_fill<float>(void*, int64_t, double, cudaStream_t, int64_t*);
+template void launch_fill<double>(void*, int64_t, double, cudaStream_t, int64_t*);
+
 // posterior mean (variance, standard deviation, coefficient of variation)
 // pooled over the chains of one problem
 __global__ void k_mean(const double* sum, int n_chains, int64_t stride, int Wo, int crop_r, int oh, int ow,

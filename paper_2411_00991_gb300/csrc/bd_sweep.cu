@@ -75,17 +75,21 @@ __device__ __forceinline__ void twiddle(const T* tw, const Shape& sh, int kl, in
 constexpr int kMaxPx = 4;   // window pixels per thread fetched in one batch
 
 // a2: the proposal of one update from its Philox counter (m, t, chain, 0):
-// z standard normal (Box-Muller), log u, rho' = rho exp(step z).
+// z standard normal (Box-Muller), log u, the log-space move hz = s_m z (s_m
+// the pixel's scale: its adapted one, else the problem's step) and
+// rho' = rho exp(hz); hz is also the Hastings term of the decision.
 template <typename T>
-__device__ __forceinline__ void proposal(const Image& im, const Chain& ch, int m, int t, T r_old, T& z, T& lu,
+__device__ __forceinline__ void proposal(const Image& im, const Chain& ch, int m, int t, T r_old, T& hz, T& lu,
                                          T& r_new, T& delta)
 {
     using P = Prec<T>;
     const uint4 x = philox4x32_10(make_uint4((uint32_t)m, (uint32_t)t, (uint32_t)ch.chain, 0u), im.seed_lo,
                                   im.seed_hi);
-    z = P::gauss(uniform23<T>(x.x), uniform23<T>(x.y));
+    const T z = P::gauss(uniform23<T>(x.x), uniform23<T>(x.y));
+    const T sm = ch.steps != nullptr ? reinterpret_cast<const T*>(ch.steps)[m] : (T)im.step;
+    hz = sm * z;
     lu = P::log(uniform23<T>(x.z));
-    r_new = r_old * P::exp((T)im.step * z);
+    r_new = r_old * P::exp(hz);
     delta = r_new - r_old;
 }
 
@@ -261,7 +265,6 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     const int rounds = (npt + n_sub - 1) / n_sub;
     T* red1 = red + (size_t)(g * 8) * 4;                   // prior partials of this sub-team
     T* red2 = red + 8 * 8 * 4 + (size_t)(g * 8) * 4;       // likelihood partials
-    const T step = (T)im.step;
     const int nsteps = (ch.n_sweeps > 0 ? ch.n_sweeps : a.n_sweeps) * S2;
     int n_acc = 0;
     // with one update per team and step, a warp of the team draws the next
@@ -393,7 +396,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     bad = bad || red2[w * 4 + 1] != (T)0;
                 }
                 const T dP = sP + (T)(sh.K - 1) * P::log1p(sS / sA);
-                const bool accept = !bad && (lu < dL + dP + step * z);
+                const bool accept = !bad && (lu < dL + dP + z);   // z holds s_m z
                 if (accept) {
                     const bool one_batch = LL <= NT * kMaxPx;
                     for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
@@ -440,6 +443,12 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     }
                 }
                 if (ch.acc_log != nullptr && lt == 0) ch.acc_log[(size_t)(t - 1) * im.Ho * im.Wo + m] = accept ? 1 : 0;
+                if (ch.steps != nullptr && t <= im.burn_in && lt == 0) {
+                    // burn-in adaptation of the pixel's proposal scale
+                    T* sg = reinterpret_cast<T*>(ch.steps);
+                    const T sn = sg[m] * (T)im.adapt_fac[2 * (t - 1) + (accept ? 0 : 1)];
+                    sg[m] = sn < (T)1e-4 ? (T)1e-4 : sn > (T)4 ? (T)4 : sn;
+                }
             }
             __syncthreads();
         }

@@ -44,7 +44,7 @@ struct ProbHost {
     int max_nhalf = 0;
     // arena offsets (bytes)
     size_t o_K64, o_K32, o_dat64, o_dat32, o_ekl, o_wa64, o_m64, o_wa32, o_m32, o_tw64, o_tw32, o_poff;
-    size_t o_sum, o_sq, o_scr, o_samp;
+    size_t o_sum, o_sq, o_scr, o_samp, o_adapt;
     int samp_first = 0;         // first valid kept-object slot (after a resume)
     size_t scr_doubles;
     int chain0;
@@ -65,7 +65,7 @@ struct Group {
 };
 
 struct ChainHost {
-    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace, o_tdev;
+    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace, o_tdev, o_steps;
 };
 
 }  // namespace
@@ -162,6 +162,8 @@ bdecon_status validate(const bdecon_problem& p, int idx)
         return fail(nullptr, BDECON_ERR_INVALID, "problem %d: stride %d must be in [L=%d, %d]", idx, S, p.L, kMaxS);
     if (p.n_chains < 1 || p.n_chains > 4096) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: n_chains %d", idx, p.n_chains);
     if (p.team_warps < 0 || p.team_warps > 8) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: team_warps %d", idx, p.team_warps);
+    if (!(p.adapt_target >= 0.0 && p.adapt_target < 1.0))
+        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: adapt_target must be in [0, 1)", idx);
     if (p.n_samples < 0 || p.sample_every < 0)
         return fail(nullptr, BDECON_ERR_INVALID, "problem %d: n_samples %d / sample_every %d must be >= 0", idx, p.n_samples,
                     p.sample_every);
@@ -453,6 +455,8 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
         ph.o_sum = A.take(8 * nobj * ph.p.n_chains);
         ph.o_sq = (ph.p.flags & BDECON_FLAG_SECOND_MOMENT) ? A.take(8 * nobj * ph.p.n_chains) : 0;
         ph.o_samp = ph.p.n_samples > 0 ? A.take(ts * nobj * (size_t)ph.p.n_samples * ph.p.n_chains) : 0;
+        const bool adapt = ph.p.adapt_target > 0.0 && ph.p.burn_in > 0;
+        ph.o_adapt = adapt ? A.take(16 * (size_t)ph.p.burn_in) : 0;
         const size_t nblk = (npix + kRedThreads - 1) / kRedThreads;
         ph.scr_doubles = std::max(nblk + (size_t)ph.n_patches + 8, nblk + 8 + 2 * (size_t)kMaxS * kMaxS) + 8;
         ph.o_scr = A.take(8 * ph.scr_doubles);
@@ -473,6 +477,7 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
             x.o_astep = A.take(4 * (size_t)ph.n_patches);
             x.o_trace = A.take(8 * ((size_t)max_sweeps + 1));
             x.o_tdev = A.take(4);
+            x.o_steps = adapt ? A.take(ts * nobj) : 0;
             chh.push_back(x);
         }
     }
@@ -601,6 +606,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         im.max_nhalf = ph.max_nhalf;
         im.sample_every = ph.p.sample_every > 0 ? ph.p.sample_every : 1;
         im.n_samples = ph.p.n_samples;
+        im.adapt_fac = ph.o_adapt ? (const double*)(A + ph.o_adapt) : nullptr;
     }
     h->chains.resize(h->chh.size());
     for (int k = 0; k < n; ++k) {
@@ -626,6 +632,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
             ch.tdev = (int*)(A + x.o_tdev);
             ch.samples = ph.o_samp ? A + ph.o_samp + (h->precision == BDECON_FP32 ? 4 : 8) * nobj * ph.p.n_samples * c
                                    : nullptr;
+            ch.steps = x.o_steps ? A + x.o_steps : nullptr;
         }
     }
     if (cudaMemcpyAsync(h->d_imgs, h->imgs.data(), sizeof(Image) * n, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
@@ -636,6 +643,26 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         if (cudaMemcpyAsync(h->arena + ph.o_ekl, ph.ent_kl.data(), 4 * ph.ent_kl.size(), cudaMemcpyHostToDevice, h->st) != cudaSuccess ||
             cudaMemcpyAsync(h->arena + ph.o_poff, ph.patch_off.data(), 8 * ph.patch_off.size(), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
             return bail(fail(h, BDECON_ERR_CUDA, "table upload"));
+        if (ph.o_adapt) {
+            // proposal-scale factors of each burn-in sweep t: exp(g (1 - a*)) after an
+            // accept, exp(-g a*) after a reject, g = 0.5 / sqrt(t)
+            std::vector<double> fac(2 * (size_t)ph.p.burn_in);
+            const double a = ph.p.adapt_target;
+            for (int t = 1; t <= ph.p.burn_in; ++t) {
+                const double g = 0.5 / std::sqrt((double)t);
+                fac[2 * (t - 1)] = std::exp(g * (1.0 - a));
+                fac[2 * (t - 1) + 1] = std::exp(-g * a);
+            }
+            if (cudaMemcpy(h->arena + ph.o_adapt, fac.data(), 8 * fac.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(h, BDECON_ERR_CUDA, "table upload"));
+        }
+        for (int c = 0; c < ph.p.n_chains; ++c) {
+            const Chain& ch = h->chains[ph.chain0 + c];
+            if (!ch.steps) continue;
+            const int64_t nobj = (int64_t)ph.Ho * ph.Wo;
+            if (h->precision == BDECON_FP32) launch_fill<float>(ch.steps, nobj, ph.p.step, h->st, &h->launches);
+            else launch_fill<double>(ch.steps, nobj, ph.p.step, h->st, &h->launches);
+        }
     }
     // per problem: upload inputs (host -> device), set-up kernels, initial objects, refresh
     for (int k = 0; k < n; ++k) {
@@ -1172,6 +1199,25 @@ bdecon_status bdecon_get_state(bdecon_handle* h, int32_t p, int32_t c, double* r
         if (h->precision == BDECON_FP32) launch_convert<float>(h->chains[ci].rho, h->d_up, n, ph.Ho, ph.Wo, ph.Wo, h->st, &h->launches);
         else launch_convert<double>(h->chains[ci].rho, h->d_up, n, ph.Ho, ph.Wo, ph.Wo, h->st, &h->launches);
         CK(h, cudaMemcpyAsync(rho, h->d_up, 8 * (size_t)n, cudaMemcpyDeviceToHost, h->st));
+    }
+    return check_device(h);
+}
+
+bdecon_status bdecon_get_steps(bdecon_handle* h, int32_t p, int32_t c, double* out)
+{
+    if (!h || !out) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    const ProbHost& ph = h->probs[p];
+    const int64_t n = (int64_t)ph.Ho * ph.Wo;
+    const Chain& ch = h->chains[ci];
+    if (ch.steps) {
+        if (h->precision == BDECON_FP32) launch_convert<float>(ch.steps, h->d_up, n, ph.Ho, ph.Wo, ph.Wo, h->st, &h->launches);
+        else launch_convert<double>(ch.steps, h->d_up, n, ph.Ho, ph.Wo, ph.Wo, h->st, &h->launches);
+        CK(h, cudaMemcpyAsync(out, h->d_up, 8 * (size_t)n, cudaMemcpyDeviceToHost, h->st));
+    } else {
+        for (int64_t k = 0; k < n; ++k) out[k] = ph.p.step;
     }
     return check_device(h);
 }

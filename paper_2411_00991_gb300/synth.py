@@ -48,6 +48,7 @@ class Problem:
     team_warps: int = 0          # 0 -> chosen by the library from the problem alone
     sample_every: int = 0        # keep every k-th post-burn-in object (0 -> 1)
     n_samples: int = 0           # kept objects per chain (0 -> none)
+    adapt_target: float = 0.0    # > 0: adapt each pixel's proposal scale during burn-in toward this acceptance
 
     @property
     def H(self) -> int:
