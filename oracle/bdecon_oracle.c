@@ -33,6 +33,11 @@
  * gain g_t = 0.5 / sqrt(t) of sweep t shrinking over burn-in, so that log s_m
  * settles where the pixel's acceptance rate is a*; after burn-in the scales
  * stay fixed and the chain is an ordinary Metropolis-Hastings chain.
+ * Optional photon-count augmentation (the paper's completed likelihood,
+ * Eq. 5): the photon counts phi_n are kept as variables and each sweep first
+ * draws every phi_n from p(phi | w_n, mu_n), then updates rho against the
+ * Poisson likelihood sum_n phi_n log mu_n - mu_n; the rho-marginal of the
+ * augmented chain's target is Eq. 9.
  */
 #include <math.h>
 #include <stdint.h>
@@ -62,6 +67,7 @@ typedef struct {
     int refresh_every;   /* recompute mu and spectra every this many sweeps    */
     double adapt_target; /* > 0: adapt the per-pixel proposal scale during
                             burn-in toward this acceptance rate               */
+    int aug;             /* photon-count augmented sampler                     */
 } or_problem;
 
 #define OR_ADAPT_GAIN 0.5
@@ -174,6 +180,58 @@ double or_loglik(double w, double o, double G, double var, double mu)
         s += exp(t - tm);
     }
     return -0.5 * log(2.0 * M_PI * var) - mu + tm + log(s);
+}
+
+/* Draw a photon count from p(phi | w, mu) ∝ Normal(w; G phi + o, var)
+ * Poisson(phi; mu) (the summands of Eq. 6, normalised) by inverse CDF: the
+ * smallest phi whose cumulative weight, summed upward from the lowest
+ * retained count, reaches u times the total.  Counts whose summand falls
+ * below 2^-60 of the largest are dropped, as in or_loglik.               */
+long or_sample_phi(double w, double o, double G, double var, double mu, double u)
+{
+    const double lmu = log(mu);
+    double c = (w - o) / G;
+    long phi = c > 0.0 ? (long)floor(c) : 0;
+    double tm = summand(w, o, G, var, lmu, phi);
+    for (;;) {
+        double tu = summand(w, o, G, var, lmu, phi + 1);
+        if (tu > tm) { ++phi; tm = tu; } else break;
+    }
+    for (;;) {
+        if (phi == 0) break;
+        double td = summand(w, o, G, var, lmu, phi - 1);
+        if (td > tm) { --phi; tm = td; } else break;
+    }
+    const double cut = tm - 60.0 * M_LN2;
+    long lo = phi, hi = phi;
+    while (lo > 0 && summand(w, o, G, var, lmu, lo - 1) >= cut) --lo;
+    while (summand(w, o, G, var, lmu, hi + 1) >= cut) ++hi;
+    double Z = 0.0;
+    for (long k = lo; k <= hi; ++k) Z += exp(summand(w, o, G, var, lmu, k) - tm);
+    double acc = 0.0;
+    for (long k = lo; k <= hi; ++k) {
+        acc += exp(summand(w, o, G, var, lmu, k) - tm);
+        if (acc >= u * Z) return k;
+    }
+    return hi;
+}
+
+/* The uniform of the photon-count draw of camera pixel n at sweep t: first
+ * Philox output of counter (n, t, chain, 1).                              */
+double or_phi_uniform(uint64_t seed, uint32_t n, uint32_t t, uint32_t chain)
+{
+    uint32_t ctr[4] = {n, t, chain, 1u};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    or_philox4x32_10(ctr, key, x);
+    return or_uniform(x[0]);
+}
+
+/* log of one pixel's completed likelihood (Eq. 5):
+ * log Normal(w; G phi + o, var) + log Poisson(phi; mu).                   */
+double or_logjoint_pixel(double w, double o, double G, double var, double mu, long phi)
+{
+    return -0.5 * log(2.0 * M_PI * var) + summand(w, o, G, var, log(mu), phi) - mu;
 }
 
 /* ------------------------------------------------------- convolution ---- */
@@ -295,6 +353,24 @@ double or_log_posterior(const or_problem* P, const double* rho)
     return ll + lp;
 }
 
+/* Log of the augmented joint density p(w, phi, rho) (prior without B(alpha)):
+ * sum_n log Normal(w_n; G phi_n + o_n, var_n) Poisson(phi_n; mu_n) + the
+ * patch log priors.                                                         */
+double or_log_joint(const or_problem* P, const double* rho, const double* phi)
+{
+    const int H = P->H, W = P->W, L = P->L;
+    double* K = (double*)malloc((size_t)L * L * sizeof(double));
+    double* mu = (double*)malloc((size_t)H * W * sizeof(double));
+    normalised_psf(P, K);
+    or_convolve(rho, H, W, K, L, mu);
+    double ll = 0.0;
+    for (int n = 0; n < H * W; ++n)
+        ll += or_logjoint_pixel(P->w[n], P->offset[n], P->gain[n], P->var[n], mu[n], (long)phi[n]);
+    double lp = log_prior_all(P, K, rho);
+    free(K); free(mu);
+    return ll + lp;
+}
+
 /* Initial object: rho0_m = b0 exp(z_m / 10), b0 = max(0.1, mean_n (w_n - o_n) / G_n),
  * z_m the Box-Muller normal of counter (m, 0, chain, 0) (sweep 0 is never a
  * sampling sweep).  The jitter keeps every patch spectrum coefficient away
@@ -326,6 +402,7 @@ typedef struct {
     double* tre;      /* scratch ph*pw                                    */
     double* tim;
     double* steps;    /* per-pixel proposal scale, Ho*Wo                  */
+    double* phi;      /* photon counts, H*W (augmented sampler)           */
 } chain_state;
 
 static void cs_refresh(chain_state* c)
@@ -373,6 +450,7 @@ static void cs_open(chain_state* c, const or_problem* P, const double* rho_in)
     c->tim = (double*)malloc((size_t)c->S * c->S * sizeof(double));
     c->steps = (double*)malloc((size_t)c->Ho * c->Wo * sizeof(double));
     for (int m = 0; m < c->Ho * c->Wo; ++m) c->steps[m] = P->step;
+    c->phi = (double*)calloc((size_t)P->H * P->W, sizeof(double));
     cs_refresh(c);
 }
 
@@ -381,7 +459,7 @@ static void cs_close(chain_state* c)
     int np = c->npi * c->npj;
     for (int p = 0; p < np; ++p) { free(c->sre[p]); free(c->sim[p]); free(c->alpha[p]); }
     free(c->sre); free(c->sim); free(c->alpha);
-    free(c->K); free(c->rho); free(c->mu); free(c->tre); free(c->tim); free(c->steps);
+    free(c->K); free(c->rho); free(c->mu); free(c->tre); free(c->tim); free(c->steps); free(c->phi);
 }
 
 /* Likelihood and prior changes for replacing rho_m (m = (i, j)) by rho_new
@@ -405,8 +483,11 @@ static int cs_delta(chain_state* c, int i, int j, double rho_new, double* dL, do
             double mu_old = c->mu[n];
             double mu_new = mu_old + delta * c->K[(a - i + 2 * R) * L + (b - j + 2 * R)];
             if (!(mu_new > 0.0)) { ok = 0; continue; }
-            l += or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu_new)
-               - or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu_old);
+            if (P->aug)   /* completed likelihood: the phi-dependent Poisson part */
+                l += c->phi[n] * (log(mu_new) - log(mu_old)) - (mu_new - mu_old);
+            else
+                l += or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu_new)
+                   - or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu_old);
         }
     }
     /* Eq. 8 for the one patch containing (i, j): the DFT is linear, so the
@@ -545,7 +626,7 @@ int or_single_update(const or_problem* P, const double* rho, int m, int t, int* 
 int or_run(const or_problem* P, int t0, int T, int order, const double* rho_in,
            double* rho_out, double* mu_out, double* sum_out, int* n_sum,
            double* trace, uint8_t* acc_log, double* samples, int64_t* n_acc,
-           double* steps_out)
+           double* steps_out, double* phi_out)
 {
     chain_state c;
     cs_open(&c, P, rho_in);
@@ -558,6 +639,10 @@ int or_run(const or_problem* P, int t0, int T, int order, const double* rho_in,
         /* this sweep's adaptation factors (burn-in sweeps only) */
         const double gain = OR_ADAPT_GAIN / sqrt((double)t);
         const double up = exp(gain * (1.0 - P->adapt_target)), down = exp(-gain * P->adapt_target);
+        if (P->aug)   /* step (1): the photon counts given the current mu */
+            for (int n = 0; n < P->H * P->W; ++n)
+                c.phi[n] = (double)or_sample_phi(P->w[n], P->offset[n], P->gain[n], P->var[n], c.mu[n],
+                                                 or_phi_uniform(P->seed, (uint32_t)n, (uint32_t)t, (uint32_t)P->chain));
         for (int u = 0; u < S; ++u)
             for (int v = 0; v < S; ++v) {
                 int ni = (Ho - 1 - u) / S + 1, nj = (Wo - 1 - v) / S + 1;
@@ -586,13 +671,14 @@ int or_run(const or_problem* P, int t0, int T, int order, const double* rho_in,
             ++ns;
         }
         if (P->refresh_every > 0 && t % P->refresh_every == 0) cs_refresh(&c);
-        if (trace) trace[tt - 1] = or_log_posterior(P, c.rho);
+        if (trace) trace[tt - 1] = P->aug ? or_log_joint(P, c.rho, c.phi) : or_log_posterior(P, c.rho);
         if (samples) memcpy(samples + (size_t)(tt - 1) * Ho * Wo, c.rho, (size_t)Ho * Wo * sizeof(double));
         if (n_acc) n_acc[tt - 1] = acc;
     }
     if (rho_out) memcpy(rho_out, c.rho, (size_t)Ho * Wo * sizeof(double));
     if (mu_out) memcpy(mu_out, c.mu, (size_t)P->H * P->W * sizeof(double));
     if (steps_out) memcpy(steps_out, c.steps, (size_t)Ho * Wo * sizeof(double));
+    if (phi_out) memcpy(phi_out, c.phi, (size_t)P->H * P->W * sizeof(double));
     if (n_sum) *n_sum = ns;
     cs_close(&c);
     return 0;

@@ -39,7 +39,8 @@ class OrProblem(C.Structure):
                 ("w", C.c_void_p), ("gain", C.c_void_p), ("offset", C.c_void_p),
                 ("var", C.c_void_p), ("psf", C.c_void_p),
                 ("seed", C.c_uint64), ("chain", C.c_int), ("step", C.c_double),
-                ("burn_in", C.c_int), ("refresh_every", C.c_int), ("adapt_target", C.c_double)]
+                ("burn_in", C.c_int), ("refresh_every", C.c_int), ("adapt_target", C.c_double),
+                ("aug", C.c_int)]
 
 
 def lib():
@@ -61,12 +62,20 @@ def lib():
         L.or_log_prior_patch.restype = C.c_double
         L.or_log_posterior.argtypes = [C.POINTER(OrProblem), C.c_void_p]
         L.or_log_posterior.restype = C.c_double
+        L.or_log_joint.argtypes = [C.POINTER(OrProblem), C.c_void_p, C.c_void_p]
+        L.or_log_joint.restype = C.c_double
+        L.or_sample_phi.argtypes = [C.c_double] * 6
+        L.or_sample_phi.restype = C.c_long
+        L.or_phi_uniform.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32]
+        L.or_phi_uniform.restype = C.c_double
+        L.or_logjoint_pixel.argtypes = [C.c_double] * 5 + [C.c_long]
+        L.or_logjoint_pixel.restype = C.c_double
         L.or_init.argtypes = [C.POINTER(OrProblem), C.c_void_p]
         L.or_delta.argtypes = [C.POINTER(OrProblem), C.c_void_p, C.c_int, C.c_double, dp, dp]
         L.or_delta.restype = C.c_int
         L.or_run.argtypes = [C.POINTER(OrProblem), C.c_int, C.c_int, C.c_int, C.c_void_p,
                              C.c_void_p, C.c_void_p, C.c_void_p, ip, C.c_void_p, C.c_void_p,
-                             C.c_void_p, C.c_void_p, C.c_void_p]
+                             C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.or_run.restype = C.c_int
         L.or_single_update.argtypes = [C.POINTER(OrProblem), C.c_void_p, C.c_int, C.c_int, ip, dp, dp, dp]
         L.or_single_update.restype = C.c_int
@@ -99,6 +108,19 @@ def draw(seed: int, m: int, t: int, chain: int):
     z, u = C.c_double(), C.c_double()
     lib().or_draw(int(seed), int(m), int(t), int(chain), C.byref(z), C.byref(u))
     return z.value, u.value
+
+
+def sample_phi(w, o, G, var, mu, u) -> int:
+    """Photon count drawn from p(phi | w, mu) by inverse CDF at u."""
+    return int(lib().or_sample_phi(float(w), float(o), float(G), float(var), float(mu), float(u)))
+
+
+def phi_uniform(seed, n, t, chain) -> float:
+    return lib().or_phi_uniform(int(seed), int(n), int(t), int(chain))
+
+
+def logjoint_pixel(w, o, G, var, mu, phi) -> float:
+    return lib().or_logjoint_pixel(float(w), float(o), float(G), float(var), float(mu), int(phi))
 
 
 def loglik(w, o, G, var, mu) -> float:
@@ -153,8 +175,15 @@ class Oracle:
         self.psf = np.ascontiguousarray(prob.psf, dtype=np.float64)
         self.c = OrProblem(prob.H, prob.W, prob.L, prob.S, _p(self.w), _p(self.g), _p(self.o),
                            _p(self.v), _p(self.psf), int(prob.seed), int(chain), float(prob.step),
-                           int(prob.burn_in), int(prob.refresh_every), float(getattr(prob, "adapt_target", 0.0)))
+                           int(prob.burn_in), int(prob.refresh_every), float(getattr(prob, "adapt_target", 0.0)),
+                           int(bool(getattr(prob, "augmented", False))))
         self.Ho, self.Wo = prob.object_shape()
+
+    def log_joint(self, rho: np.ndarray, phi: np.ndarray) -> float:
+        """Log of the augmented joint density p(w, phi, rho) (Eq. 5 with the prior)."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        return lib().or_log_joint(C.byref(self.c), _p(rho), _p(phi))
 
     def log_posterior(self, rho: np.ndarray) -> float:
         rho = np.ascontiguousarray(rho, dtype=np.float64)
@@ -190,14 +219,15 @@ class Oracle:
         acc = np.empty((T, Ho, Wo), dtype=np.uint8) if want_acc_log else None
         smp = np.empty((T, Ho, Wo)) if want_samples else None
         steps = np.empty((Ho, Wo))
+        phi = np.empty((H, W))
         ns = C.c_int()
         rin = None if rho_in is None else np.ascontiguousarray(rho_in, dtype=np.float64)
         lib().or_run(C.byref(self.c), int(t0), int(T), int(order), _p(rin), _p(rho_out), _p(mu_out),
-                     _p(sum_out), C.byref(ns), _p(trace), _p(acc), _p(smp), _p(n_acc), _p(steps))
+                     _p(sum_out), C.byref(ns), _p(trace), _p(acc), _p(smp), _p(n_acc), _p(steps), _p(phi))
         n = ns.value
         return dict(rho=rho_out, mu=mu_out, sum=sum_out, n_sum=n,
                     mean=(sum_out / n if n > 0 else None), trace=trace, acc_log=acc,
-                    samples=smp, n_acc=n_acc, steps=steps)
+                    samples=smp, n_acc=n_acc, steps=steps, phi=phi)
 
 
 if __name__ == "__main__":

@@ -49,6 +49,7 @@ class Problem:
     sample_every: int = 0        # keep every k-th post-burn-in object (0 -> 1)
     n_samples: int = 0           # kept objects per chain (0 -> none)
     adapt_target: float = 0.0    # > 0: adapt each pixel's proposal scale during burn-in toward this acceptance
+    augmented: bool = False      # photon-count augmented sampler (completed likelihood, Eq. 5)
 
     @property
     def H(self) -> int:
