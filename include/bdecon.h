@@ -116,6 +116,13 @@ typedef struct {
 #define BDECON_FLAG_ACCEPT_LOG 1   /* keep the accept decision of every update of
                                       every sweep (max_sweeps x object bytes; testing) */
 #define BDECON_FLAG_SECOND_MOMENT 2 /* also accumulate sum of rho^2 (uncertainty)  */
+#define BDECON_FLAG_AUGMENTED 4    /* photon-count augmented sampler: each sweep first
+                                      draws every camera pixel's photon count phi_n from
+                                      p(phi | w_n, mu_n) (the completed likelihood of
+                                      Eq. 5), then updates rho against the Poisson
+                                      likelihood sum_n phi_n log mu_n - mu_n; the rho-
+                                      marginal of its target is Eq. 9.  Its trace is the
+                                      log of the joint density p(w, phi, rho).      */
 
 /* ------------------------------------------------------------- lifetime */
 
@@ -179,6 +186,10 @@ bdecon_status bdecon_posterior_var(bdecon_handle* h, int32_t p, double* out, int
  * (the paper's relative uncertainty map).                                  */
 bdecon_status bdecon_posterior_std(bdecon_handle* h, int32_t p, double* out, int32_t crop);
 bdecon_status bdecon_posterior_cv(bdecon_handle* h, int32_t p, double* out, int32_t crop);
+
+/* Photon counts phi_n of chain c of an augmented problem (H*W doubles):
+ * those of the last sweep (or of the initial draw).                        */
+bdecon_status bdecon_get_phi(bdecon_handle* h, int32_t p, int32_t c, double* out);
 
 /* Per-pixel proposal scales of chain c of problem p, (H+2R)*(W+2R)
  * doubles: the adapted s_m (see adapt_target), else `step` everywhere.   */

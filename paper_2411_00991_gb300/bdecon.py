@@ -21,6 +21,7 @@ BDECON_FP64 = 0
 BDECON_FP32 = 1
 FLAG_ACCEPT_LOG = 1
 FLAG_SECOND_MOMENT = 2
+FLAG_AUGMENTED = 4
 
 STATUS = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "TIMEOUT", 5: "STATE", 6: "NUMERIC"}
 
@@ -59,7 +60,7 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_server_submit", "bdecon_server_poll", "bdecon_server_wait", "bdecon_server_stats",
            "bdecon_server_stop", "bdecon_set_grouping", "bdecon_autotune", "bdecon_set_graph",
            "bdecon_posterior_std", "bdecon_posterior_cv", "bdecon_get_samples", "bdecon_posterior_quantiles",
-           "bdecon_get_steps"]
+           "bdecon_get_steps", "bdecon_get_phi"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -101,6 +102,7 @@ def load(build_if_missing: bool = True):
         "bdecon_set_state": [H, i32, i32, vp, i64],
         "bdecon_get_mu": [H, i32, i32, vp],
         "bdecon_get_steps": [H, i32, i32, vp],
+        "bdecon_get_phi": [H, i32, i32, vp],
         "bdecon_log_posterior": [H, i32, i32, dp],
         "bdecon_delta": [H, i32, i32, i64, C.c_double, dp, dp, C.POINTER(i32)],
         "bdecon_set_plan": [H, i32, i32, i32, i32],
@@ -161,7 +163,8 @@ def _problem(pr, precision, max_sweeps, flags, keep) -> _Problem:
     return _Problem(H, W, _p(img), psf.shape[0], _p(psf), _p(g), gs, _p(o), os_, _p(v), vs,
                     int(pr.stride), int(pr.n_chains), int(pr.seed), float(pr.step),
                     int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
-                    int(flags), int(getattr(pr, "team_warps", 0)), int(getattr(pr, "sample_every", 0)),
+                    int(flags) | (FLAG_AUGMENTED if getattr(pr, "augmented", False) else 0),
+                    int(getattr(pr, "team_warps", 0)), int(getattr(pr, "sample_every", 0)),
                     int(getattr(pr, "n_samples", 0)), float(getattr(pr, "adapt_target", 0.0)))
 
 
@@ -336,6 +339,13 @@ class Sampler:
     def set_state(self, rho: np.ndarray, sweeps: int, p: int = 0, c: int = 0):
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         self._ck(self.L.bdecon_set_state(self.h, p, c, _p(rho), int(sweeps)))
+
+    def get_phi(self, p: int = 0, c: int = 0) -> np.ndarray:
+        """Photon counts of an augmented chain, (H, W)."""
+        H, W, Ho, Wo = self._shape(p)
+        out = np.empty((H, W))
+        self._ck(self.L.bdecon_get_phi(self.h, p, c, _p(out)))
+        return out
 
     def get_steps(self, p: int = 0, c: int = 0) -> np.ndarray:
         """Per-pixel proposal scales (adapted during burn-in when adapt_target > 0)."""

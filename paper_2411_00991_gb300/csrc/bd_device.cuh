@@ -188,6 +188,68 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
     return __all_sync(0xffffffffu, ok);
 }
 
+// ------------------------------------------- photon-count augmentation --
+// Draw of a photon count from p(phi | w, mu) ∝ exp(-(c - phi)^2 is2 / 2)
+// mu^phi / phi!  (the summands of Eq. 6: Normal(w; G phi + o, var) times
+// Poisson(phi; mu), in photon units) by inverse CDF at u.  With
+// g(phi) = log(T_{phi+1} / T_phi) = is2 (c - phi - 1/2) + log mu - log(phi + 1),
+// decreasing in phi (the summand is log-concave), the integer mode is reached
+// by stepping from the Gaussian-approximation centre; terms relative to the
+// mode are kept while above 2^-60 of it (double) or 2^-30 (float), and the
+// cumulative weight is summed upward from the lowest kept count.  Sets
+// status when a walk would exceed kPhiSteps terms.
+constexpr int kPhiSteps = 1 << 16;
+
+template <typename T>
+__device__ __forceinline__ int sample_phi(T mu, T c, T is2, T u, int& status)
+{
+    using P = Prec<T>;
+    const T lmu = P::log(mu);
+    const T cut = sizeof(T) == 8 ? (T)(-60.0 * 0.69314718055994531) : (T)(-30.0 * 0.69314718055994531);
+    T f0 = mu * (c * is2 + (T)1) / (mu * is2 + (T)1);
+    f0 = f0 < (T)1.0e7 ? f0 : (T)1.0e7;
+    int m = f0 > (T)0 ? (int)f0 : 0;
+    int it = 0;
+#define BD_G(f) (is2 * (c - (T)(f) - (T)0.5) + lmu - P::log((T)((f) + 1)))
+    while (BD_G(m) > (T)0 && it < kPhiSteps) { ++m; ++it; }
+    while (m > 0 && BD_G(m - 1) < (T)0 && it < kPhiSteps) { --m; ++it; }
+    T Z = (T)1, l = (T)0, llo = (T)0;
+    int lo = m, hi = m;
+    for (int f = m - 1; f >= 0 && it < kPhiSteps; --f, ++it) {   // log T_f - log T_m
+        l -= BD_G(f);
+        if (l < cut) break;
+        Z += P::exp(l);
+        lo = f;
+        llo = l;
+    }
+    l = (T)0;
+    for (int f = m; it < kPhiSteps; ++f, ++it) {                  // log T_{f+1} - log T_m
+        l += BD_G(f);
+        if (l < cut) break;
+        Z += P::exp(l);
+        hi = f + 1;
+    }
+    if (it >= kPhiSteps) status = 1;
+    const T target = u * Z;
+    T acc = (T)0;
+    l = llo;
+    for (int f = lo; f < hi; ++f) {
+        acc += P::exp(l);
+        if (acc >= target) return f;
+        l += BD_G(f);
+    }
+#undef BD_G
+    return hi;
+}
+
+// phi-dependent part of the log completed likelihood of one pixel (Eq. 5):
+// -(c - phi)^2 is2 / 2 + phi log mu - log phi!
+__device__ __forceinline__ double phi_logterm(int phi, double lmu, double c, double is2)
+{
+    const double d = c - (double)phi;
+    return -0.5 * d * d * is2 + (double)phi * lmu - lgamma((double)phi + 1.0);
+}
+
 // Integer mode estimate of the photon posterior (log-concave in phi): the
 // Gaussian-approximation centre mu (c + s^2) / (mu + s^2), then one Newton
 // step on d/dphi log T_phi ~ (c - phi)/s^2 + log(mu / (phi + 1/2)).  Any

@@ -79,6 +79,7 @@ struct Chain {
     int n_sweeps;                    // sweeps of this chain in the launch (0: the launch's n_sweeps)
     void* samples;                   // [n_samples][Ho*Wo] T kept objects, or null
     void* steps;                     // [Ho*Wo] T per-pixel proposal scales (adapting problems), or null
+    void* phi;                       // [H*mu_pitch] T photon counts (augmented sampler), or null
 };
 
 struct SweepArgs {
@@ -86,6 +87,7 @@ struct SweepArgs {
     const Chain* chains;
     int n_chains;
     int n_sweeps;                    // sweeps in this launch (chains may take fewer)
+    int aug;                         // photon-count augmented sampler (every chain of the launch)
     int* err;
     int resident;                    // 1: tile state (data, spectra, rho) held in shared memory
     unsigned long long wait_ns;      // limit of each neighbour wait
@@ -156,12 +158,18 @@ void launch_init_rho(const Image& im, const Chain& ch, const double* b0, cudaStr
 template <typename T>
 // out_logpost receives the log posterior at out_logpost[*out_index] (index 0
 // when out_index is null)
+// (with write_state on an augmented chain, the total is the log of the joint
+// density p(w, phi, rho) at the chain's photon counts)
 void launch_refresh(const Image& im, const Chain& ch, double* scratch, int write_state,
                     double* out_logpost, const int* out_index, int* err, cudaStream_t st, int64_t* launches);
+// photon counts of every camera pixel drawn from p(phi | w, mu) with the
+// uniforms of sweep t (the augmented sampler's initial draw)
+template <typename T>
+void launch_sample_phi(const Image& im, const Chain& ch, int t, int* err, cudaStream_t st, int64_t* launches);
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 template <typename T>
-int sweep_blocks_per_sm(int threads, size_t smem);
+int sweep_blocks_per_sm(int threads, size_t smem, bool aug);
 // zero every chain's progress words, last-accept words and trace partials
 void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_slots, cudaStream_t st,
                   int64_t* launches);

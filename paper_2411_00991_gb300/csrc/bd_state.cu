@@ -225,7 +225,12 @@ __global__ void __launch_bounds__(kRedThreads) k_refresh_mu(Image im, Chain ch, 
             atomicOr(err, kErrNumeric);
         } else {
             const double* d = im.dat64 + 4 * (size_t)idx;
-            ll = loglik64(mu, d[0], d[1], d[2], d[3]);
+            if (write && ch.phi) {   // augmented chain: the completed likelihood at its counts
+                const int phi = (int)reinterpret_cast<const T*>(ch.phi)[(size_t)a * im.mu_pitch + b];
+                ll = d[3] + phi_logterm(phi, ::log((double)(T)mu), d[0], d[1]) - (double)(T)mu;
+            } else {
+                ll = loglik64(mu, d[0], d[1], d[2], d[3]);
+            }
             if (write && ch.cum) {
                 // the cache describes the stored (rounded) expected image
                 const Cum6 q = photon_cumulants<double>((double)(T)mu, d[0], d[1], d[2]);
@@ -311,6 +316,34 @@ template void launch_refresh<float>(const Image&, const Chain&, double*, int, do
                                     int64_t*);
 template void launch_refresh<double>(const Image&, const Chain&, double*, int, double*, const int*, int*, cudaStream_t,
                                      int64_t*);
+
+// ------------------------------------------------- photon-count draw -----
+template <typename T>
+__global__ void k_sample_phi(Image im, Chain ch, int t, int* err)
+{
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= im.H * im.W) return;
+    const int a = idx / im.W, b = idx % im.W;
+    const size_t k = (size_t)a * im.mu_pitch + b;
+    const T mu = reinterpret_cast<const T*>(ch.mu)[k];
+    const Dat4<T> dv = dat<T>(im)[idx];
+    const uint4 x = philox4x32_10(make_uint4((uint32_t)idx, (uint32_t)t, (uint32_t)ch.chain, 1u), im.seed_lo,
+                                  im.seed_hi);
+    int status = 0;
+    const int phi = sample_phi<T>(mu, dv.c, dv.is2, uniform23<T>(x.x), status);
+    if (status) atomicOr(err, kErrNumeric);
+    reinterpret_cast<T*>(ch.phi)[k] = (T)phi;
+}
+
+template <typename T>
+void launch_sample_phi(const Image& im, const Chain& ch, int t, int* err, cudaStream_t st, int64_t* launches)
+{
+    const int n = im.H * im.W;
+    k_sample_phi<T><<<(n + 255) / 256, 256, 0, st>>>(im, ch, t, err);
+    ++*launches;
+}
+template void launch_sample_phi<float>(const Image&, const Chain&, int, int*, cudaStream_t, int64_t*);
+template void launch_sample_phi<double>(const Image&, const Chain&, int, int*, cudaStream_t, int64_t*);
 
 // ------------------------------------------------------------ reset -----
 __global__ void k_reset(const Image* imgs, const Chain* chains, int n_slots)

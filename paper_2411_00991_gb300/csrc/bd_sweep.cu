@@ -163,11 +163,70 @@ __device__ __forceinline__ void lik_partial(const T* mu_g, const float4* cum_g, 
     }
 }
 
-template <typename T, bool RES>
+// Augmented sampler: the window's expected image and photon counts.
+template <typename T>
+__device__ __forceinline__ void window_fetch_aug(const T* mu_g, const T* phi_g, const Image& im, int i, int j,
+                                                 T (&muv)[kMaxPx], T (&phv)[kMaxPx], int k0)
+{
+    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L, NT = im.team;
+#pragma unroll
+    for (int jj = 0; jj < kMaxPx; ++jj) {
+        const int k = k0 + jj * NT;
+        const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
+        const bool in = k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W;
+        muv[jj] = in ? __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb) : (T)-1;
+        phv[jj] = in ? __ldcg(phi_g + (size_t)aa * im.mu_pitch + bb) : (T)0;
+    }
+}
+
+// Augmented sampler: the change of the Poisson part of the completed
+// likelihood (Eq. 5) over the window at the current photon counts,
+//   sum_n phi_n log(1 + delta K/mu_n) - delta K,
+// a proposal making some mu'_n <= 0 being impossible.  Same thread
+// assignment and reduction as lik_partial.
+template <typename T>
+__device__ __forceinline__ void lik_partial_aug(const T* mu_g, const T* phi_g, const T* Ks, const Image& im, int i,
+                                                int j, int lt, int NT, T delta, T (&muv)[kMaxPx], T (&phv)[kMaxPx],
+                                                T* out, int lane, bool prefetched)
+{
+    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L;
+    T accL = 0;
+    bool badL = false;
+    for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
+        if (!(prefetched && k0 == lt)) window_fetch_aug<T>(mu_g, phi_g, im, i, j, muv, phv, k0);
+#pragma unroll
+        for (int jj = 0; jj < kMaxPx; ++jj) {
+            const int k = k0 + jj * NT;
+            const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
+            if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
+                const T xk = mul_rn(delta, Ks[k]);
+                const T d = xk / muv[jj];
+                if (!(d > (T)-1)) {
+                    badL = true;
+                    continue;
+                }
+                T lg;
+                if constexpr (std::is_same<T, float>::value) lg = log1p_cum(d);
+                else lg = ::log1p(d);
+                accL += phv[jj] * lg - xk;
+            }
+        }
+    }
+    accL = warp_sum(accL);
+    const bool wb = __any_sync(0xffffffffu, badL);
+    if (lane == 0) {
+        out[0] = accL;
+        out[1] = wb ? (T)1 : (T)0;
+    }
+}
+
+template <typename T, bool RES, bool AUG>
 __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_sweep(SweepArgs a)
 {
     using P = Prec<T>;
-    constexpr bool CUM = std::is_same<T, float>::value;   // float sweeps use the cumulant cache
+    // float sweeps of the marginal sampler use the cumulant cache; the
+    // augmented sampler (AUG) scores windows from the photon counts instead
+    constexpr bool CUM = std::is_same<T, float>::value && !AUG;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_nbr[8];
     __shared__ int s_nn;
@@ -176,6 +235,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     __shared__ int s_stale;
     __shared__ int s_acc_any;
     __shared__ T s_prop[2][8][4];   // next-step proposals of one-patch teams: z, log u, rho', delta
+    __shared__ double s_phid[AUG ? 8 : 1][8];   // photon-count step: [sub-team][warp] log-density changes
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -214,6 +274,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
 
     T* rho_g = reinterpret_cast<T*>(ch.rho);
     T* mu_g = reinterpret_cast<T*>(ch.mu);
+    T* phi_g = reinterpret_cast<T*>(ch.phi);
     T* spec_g = reinterpret_cast<T*>(ch.spec);
     float4* cum_g = ch.cum;
     float2* cum2_g = ch.cum2;
@@ -265,14 +326,18 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     const int rounds = (npt + n_sub - 1) / n_sub;
     T* red1 = red + (size_t)(g * 8) * 4;                   // prior partials of this sub-team
     T* red2 = red + 8 * 8 * 4 + (size_t)(g * 8) * 4;       // likelihood partials
-    const int nsteps = (ch.n_sweeps > 0 ? ch.n_sweeps : a.n_sweeps) * S2;
+    // a sweep is S2 class steps, preceded in the augmented sampler by a
+    // photon-count step (so SS = S2 + 1 steps); cs counts class steps only
+    const int SS = AUG ? S2 + 1 : S2;
+    const int nsw = ch.n_sweeps > 0 ? ch.n_sweeps : a.n_sweeps;
+    const int nsteps = nsw * SS, ncs = nsw * S2;
     int n_acc = 0;
     // with one update per team and step, a warp of the team draws the next
     // step's proposal ahead of time (before the neighbour wait); not when a
     // patch has a single class (S = 1), where the next step revisits the pixel
     const bool ahead = rounds == 1 && S2 > 1;
     const int pwarp = nwt > 1 ? 1 : 0;   // the drawing warp: not the one that polls the flags
-    if (ahead && in_team && twarp == pwarp && g < npt && nsteps > 0) {
+    if (ahead && in_team && twarp == pwarp && g < npt && ncs > 0) {
         const int pi = pi0 + g / tw_, pj = pj0 + (g - (g / tw_) * tw_);
         const Shape& sh = im.shape[shape_index(im, pi, pj)];
         if (sh.ph > 0 && sh.pw > 0) {
@@ -287,8 +352,69 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     __syncthreads();
 
     for (int s = 0; s < nsteps; ++s) {
-        const int slot = s / S2, c = s - slot * S2;
+        const int slot = s / SS, cc = s - slot * SS;
         const int t = t0 + 1 + slot;
+        if constexpr (AUG) {
+            if (cc == 0) {
+                // a0 (augmented sampler): after the neighbours finished the previous
+                // sweep, draw the photon counts of the camera pixels centred on the
+                // tile's patches from p(phi | w, mu) (Philox counter (n, t, chain, 1));
+                // the change of the log joint density goes to the patch's trace part
+                if (s > 0 && tid < 32) {
+                    const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns);
+                    if (lane == 0 && !ok) s_abort = 1;
+                }
+                __syncthreads();
+                if (s_abort) return;
+                for (int r = 0; r < rounds; ++r) {
+                    const int q = r * n_sub + g;
+                    double dj = 0.0;
+                    int pi = 0, pj = 0;
+                    if (in_team && q < npt) {
+                        pi = pi0 + q / tw_;
+                        pj = pj0 + (q - (q / tw_) * tw_);
+                        const Shape& shp = im.shape[shape_index(im, pi, pj)];
+                        int bad = 0;
+                        for (int e = lt; e < shp.ph * shp.pw; e += NT) {
+                            const int uu = e / shp.pw, vv = e - (e / shp.pw) * shp.pw;
+                            const int aa = pi * S + uu - R, bb = pj * S + vv - R;
+                            if ((unsigned)aa >= (unsigned)H || (unsigned)bb >= (unsigned)W) continue;
+                            const size_t idx = (size_t)aa * im.mu_pitch + bb;
+                            const T mu = __ldcg(mu_g + idx);
+                            const Dat4<T> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
+                            const uint4 x = philox4x32_10(
+                                make_uint4((uint32_t)(aa * W + bb), (uint32_t)t, (uint32_t)ch.chain, 1u), im.seed_lo,
+                                im.seed_hi);
+                            const int pn = sample_phi<T>(mu, dv.c, dv.is2, uniform23<T>(x.x), bad);
+                            const int po = (int)phi_g[idx];
+                            const double lmu = ::log((double)mu);
+                            dj += phi_logterm(pn, lmu, (double)dv.c, (double)dv.is2) -
+                                  phi_logterm(po, lmu, (double)dv.c, (double)dv.is2);
+                            phi_g[idx] = (T)pn;
+                        }
+                        if (bad) atomicOr(a.err, kErrNumeric);
+                        dj = warp_sum(dj);
+                        if (lane == 0) s_phid[g][twarp] = dj;
+                    }
+                    __syncthreads();
+                    if (in_team && q < npt && lt == 0) {
+                        double tot = 0.0;
+                        for (int w = 0; w < nwt; ++w) tot += s_phid[g][w];
+                        ch.trace_part[(size_t)slot * im.n_patches + pi * im.npj + pj] += tot;
+                    }
+                    __syncthreads();
+                }
+                if (tid == 0 && (int)blockIdx.x != a.silent_block) {
+                    // the neighbours' next windows read these counts: mark the step
+                    // (their speculative scores are redone) and release
+                    ch.acc_step[tl] = s + 1;
+                    st_release(ch.prog + tl, s + 1);
+                }
+                continue;
+            }
+        }
+        const int c = AUG ? cc - 1 : cc;
+        const int cs = slot * S2 + c;            // class-step ordinal
         const int u = c / S, v = c - (c / S) * S;
         for (int r = 0; r < rounds; ++r) {
             const int q = r * n_sub + g;
@@ -307,18 +433,22 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             bool badP = false;
             T* spec_p = RES ? spec_s + (size_t)q * 2 * im.max_nhalf : spec_g + 2 * im.patch_off[pi * im.npj + pj];
             T muv[kMaxPx];
-            float4 cq[kMaxPx];
-            float2 cq2[kMaxPx];
+            float4 cq[AUG ? 1 : kMaxPx];
+            float2 cq2[AUG ? 1 : kMaxPx];
+            T phv[AUG ? kMaxPx : 1];
             // the window's first batch is fetched before the prior work so its
             // latency overlaps the arithmetic below
-            if (active) window_fetch<T, CUM>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, lt);
+            if (active) {
+                if constexpr (AUG) window_fetch_aug<T>(mu_g, phi_g, im, i, j, muv, phv, lt);
+                else window_fetch<T, CUM>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, lt);
+            }
             // a2 + a4: proposal and prior change (own tile state only)
             if (active) {
                 if (ahead) {
-                    z = s_prop[s & 1][g][0];
-                    lu = s_prop[s & 1][g][1];
-                    r_new = s_prop[s & 1][g][2];
-                    delta = s_prop[s & 1][g][3];
+                    z = s_prop[cs & 1][g][0];
+                    lu = s_prop[cs & 1][g][1];
+                    r_new = s_prop[cs & 1][g][2];
+                    delta = s_prop[cs & 1][g][3];
                 } else {
                     r_old = RES ? rho_s[(size_t)q * S2 + u * S + v] : rho_g[m];
                     proposal<T>(im, ch, m, t, r_old, z, lu, r_new, delta);
@@ -346,11 +476,15 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // a step this runs before the neighbour wait, on the expected image
             // as it is now; it is redone below only if a neighbouring tile
             // accepted an update since this block last waited for it.
-            if (active)
-                lik_partial<T, RES, CUM>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT, delta,
-                                         muv, red2 + twarp * 4, lane, cq, cq2, true);
-            if (ahead && in_team && twarp == pwarp && q < npt && s + 1 < nsteps) {
-                const int s1 = s + 1, c1 = s1 % S2;
+            if (active) {
+                if constexpr (AUG)
+                    lik_partial_aug<T>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane, true);
+                else
+                    lik_partial<T, RES, CUM>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
+                                             delta, muv, red2 + twarp * 4, lane, cq, cq2, true);
+            }
+            if (ahead && in_team && twarp == pwarp && q < npt && cs + 1 < ncs) {
+                const int s1 = cs + 1, c1 = s1 % S2;
                 const int u1 = c1 / S, v1 = c1 - (c1 / S) * S;
                 const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
                 const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
@@ -378,9 +512,14 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             __syncthreads();
             if (s_abort) return;
             if (r == 0 && s > 0 && s_stale) {
-                if (active)
-                    lik_partial<T, RES, CUM>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT, delta,
-                                             muv, red2 + twarp * 4, lane, cq, cq2, false);
+                if (active) {
+                    if constexpr (AUG)
+                        lik_partial_aug<T>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane,
+                                           false);
+                    else
+                        lik_partial<T, RES, CUM>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
+                                                 delta, muv, red2 + twarp * 4, lane, cq, cq2, false);
+                }
                 __syncthreads();
             }
             // a5: Metropolis-Hastings decision with the Hastings term of the log-space walk
@@ -507,7 +646,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
 
 // Raise the kernel's dynamic shared-memory limit to at least smem (the limit
 // only grows, so launches with smaller plans stay valid).
-template <typename T, bool RES>
+template <typename T, bool RES, bool AUG>
 cudaError_t ensure_smem_limit(size_t smem)
 {
     static std::atomic<size_t> limit{0};
@@ -515,7 +654,8 @@ cudaError_t ensure_smem_limit(size_t smem)
     if (limit.load() >= smem) return cudaSuccess;
     std::lock_guard<std::mutex> lock(mu);
     if (limit.load() >= smem) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_sweep<T, RES>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute((const void*)k_sweep<T, RES, AUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) limit.store(smem);
     return e;
 }
@@ -528,8 +668,10 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
 {
     SweepArgs args = a;
     void* kargs[] = {&args};
-    const void* fn = a.resident ? (const void*)k_sweep<T, true> : (const void*)k_sweep<T, false>;
-    cudaError_t e = a.resident ? ensure_smem_limit<T, true>(smem) : ensure_smem_limit<T, false>(smem);
+    const void* fn = a.aug ? (a.resident ? (const void*)k_sweep<T, true, true> : (const void*)k_sweep<T, false, true>)
+                           : (a.resident ? (const void*)k_sweep<T, true, false> : (const void*)k_sweep<T, false, false>);
+    cudaError_t e = a.aug ? (a.resident ? ensure_smem_limit<T, true, true>(smem) : ensure_smem_limit<T, false, true>(smem))
+                          : (a.resident ? ensure_smem_limit<T, true, false>(smem) : ensure_smem_limit<T, false, false>(smem));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -544,27 +686,35 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
     return cudaLaunchKernelExC(&cfg, fn, kargs);
 }
 
+// Blocks of the sweep kernel resident per SM for this block size and shared
+// memory (the smaller of its resident and streamed forms, so either fits).
 template <typename T>
-int sweep_blocks_per_sm(int threads, size_t smem)
+int sweep_blocks_per_sm(int threads, size_t smem, bool aug)
 {
-    int n = 0, n2 = 0;
-    const void* fn = (const void*)k_sweep<T, true>;
-    const void* fn2 = (const void*)k_sweep<T, false>;
-    (void)fn;
-    (void)fn2;
-    if (ensure_smem_limit<T, true>(smem) != cudaSuccess || ensure_smem_limit<T, false>(smem) != cudaSuccess) {
+    const void* fns[2] = {aug ? (const void*)k_sweep<T, true, true> : (const void*)k_sweep<T, true, false>,
+                          aug ? (const void*)k_sweep<T, false, true> : (const void*)k_sweep<T, false, false>};
+    const cudaError_t e = aug ? (ensure_smem_limit<T, true, true>(smem) == cudaSuccess ? ensure_smem_limit<T, false, true>(smem)
+                                                                                        : cudaErrorInvalidValue)
+                              : (ensure_smem_limit<T, true, false>(smem) == cudaSuccess
+                                     ? ensure_smem_limit<T, false, false>(smem)
+                                     : cudaErrorInvalidValue);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<T, true>, threads, smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_sweep<T, false>, threads, smem) != cudaSuccess) return 0;
-    return n < n2 ? n : n2;
+    int best = 1 << 30;
+    for (const void* fn : fns) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) return 0;
+        best = n < best ? n : best;
+    }
+    return best;
 }
 
 template cudaError_t launch_sweep<float>(const SweepArgs&, int, int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs&, int, int, size_t, cudaStream_t);
-template int sweep_blocks_per_sm<float>(int, size_t);
-template int sweep_blocks_per_sm<double>(int, size_t);
+template int sweep_blocks_per_sm<float>(int, size_t, bool);
+template int sweep_blocks_per_sm<double>(int, size_t, bool);
 
 // ---------------------------------------------------------------- delta --
 // The same per-update arithmetic for one hypothetical proposal (testing):

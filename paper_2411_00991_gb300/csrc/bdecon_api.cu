@@ -61,11 +61,12 @@ struct Group {
     size_t smem = 0;
     int resident = 1;
     bool streamed = false;             // plan with tile state in global memory even if it fits in shared
+    bool aug = false;                  // photon-count augmented problems (their own kernel form)
     int chain_off = 0, n_chains = 0;   // slice of the group-ordered chain table
 };
 
 struct ChainHost {
-    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace, o_tdev, o_steps;
+    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace, o_tdev, o_steps, o_phi;
 };
 
 }  // namespace
@@ -252,9 +253,10 @@ void describe(ProbHost& ph)
     ph.spec_len = off;
 }
 
-int occupancy(int prec, int threads, size_t smem)
+int occupancy(int prec, int threads, size_t smem, bool aug)
 {
-    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem) : sweep_blocks_per_sm<double>(threads, smem);
+    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug)
+                               : sweep_blocks_per_sm<double>(threads, smem, aug);
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -324,7 +326,7 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
             int tot = 0;
             for (const PlanItem* it : items) tot += item_blocks(*it);
             if (smem <= kMaxSmem) {
-                const int bps = occupancy(precision, g.threads, smem);
+                const int bps = occupancy(precision, g.threads, smem, g.aug);
                 if (bps > 0 && tot <= bps * sms) {
                     g.smem = smem;
                     g.resident = resident;
@@ -414,15 +416,18 @@ void form_groups(bdecon_handle* h)
     h->prob_group.assign(n, -1);
     for (int k = 0; k < n; ++k) {
         int gi = -1;
+        const bool aug = (h->probs[k].p.flags & BDECON_FLAG_AUGMENTED) != 0;
         for (size_t q = 0; q < h->groups.size() && gi < 0; ++q)
-            if (h->one_launch || (h->groups[q].L == h->probs[k].L && h->groups[q].S == h->probs[k].S &&
-                                  h->groups[q].team == h->imgs[k].team))
+            if (h->groups[q].aug == aug &&
+                (h->one_launch || (h->groups[q].L == h->probs[k].L && h->groups[q].S == h->probs[k].S &&
+                                   h->groups[q].team == h->imgs[k].team)))
                 gi = (int)q;
         if (gi < 0) {
             Group g;
             g.L = h->probs[k].L;
             g.S = h->probs[k].S;
             g.team = h->imgs[k].team;
+            g.aug = aug;
             h->groups.push_back(g);
             gi = (int)h->groups.size() - 1;
         }
@@ -468,8 +473,10 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
             x.o_rho = A.take(ts * nobj);
             x.o_mu = A.take(ts * (size_t)ph.H * ph.pitch);
             x.o_spec = A.take(2 * ts * (size_t)ph.spec_len);
-            x.o_cum = prec == BDECON_FP32 ? A.take(16 * (size_t)ph.H * ph.pitch) : 0;
-            x.o_cum2 = prec == BDECON_FP32 ? A.take(8 * (size_t)ph.H * ph.pitch) : 0;
+            const bool aug = (ph.p.flags & BDECON_FLAG_AUGMENTED) != 0;
+            x.o_cum = prec == BDECON_FP32 && !aug ? A.take(16 * (size_t)ph.H * ph.pitch) : 0;
+            x.o_cum2 = prec == BDECON_FP32 && !aug ? A.take(8 * (size_t)ph.H * ph.pitch) : 0;
+            x.o_phi = aug ? A.take(ts * (size_t)ph.H * ph.pitch) : 0;
             x.o_tpart = A.take(8 * (size_t)kMaxSlots * ph.n_patches);
             x.o_acc = A.take(8 * (size_t)max_sweeps);
             x.o_log = (ph.p.flags & BDECON_FLAG_ACCEPT_LOG) ? A.take((size_t)max_sweeps * nobj) : 0;
@@ -633,6 +640,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
             ch.samples = ph.o_samp ? A + ph.o_samp + (h->precision == BDECON_FP32 ? 4 : 8) * nobj * ph.p.n_samples * c
                                    : nullptr;
             ch.steps = x.o_steps ? A + x.o_steps : nullptr;
+            ch.phi = x.o_phi ? A + x.o_phi : nullptr;
         }
     }
     if (cudaMemcpyAsync(h->d_imgs, h->imgs.data(), sizeof(Image) * n, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
@@ -694,6 +702,13 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         for (int c = 0; c < p.n_chains; ++c) {
             const Chain& ch = h->chains[ph.chain0 + c];
             if (refresh(h, ph.chain0 + c, 1, ch.trace) != BDECON_OK) return bail(BDECON_ERR_CUDA);
+            if (ch.phi) {
+                // augmented sampler: photon counts drawn at the initial mu (uniforms
+                // of sweep 0), then the trace starts at the joint density
+                if (h->precision == BDECON_FP32) launch_sample_phi<float>(h->imgs[k], ch, 0, h->d_err, h->st, &h->launches);
+                else launch_sample_phi<double>(h->imgs[k], ch, 0, h->d_err, h->st, &h->launches);
+                if (refresh(h, ph.chain0 + c, 1, ch.trace) != BDECON_OK) return bail(BDECON_ERR_CUDA);
+            }
         }
     }
     form_groups(h);
@@ -805,6 +820,7 @@ bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle
         a.imgs = ls.d_imgs; a.chains = ls.d_gch + g.chain_off; a.n_chains = g.n_chains;
         a.n_sweeps = len; a.err = eh->d_err; a.resident = g.resident;
         a.wait_ns = eh->wait_ns; a.silent_block = gi == 0 ? eh->silent_block : -1;
+        a.aug = g.aug ? 1 : 0;
         cudaError_t e = eh->precision == BDECON_FP32 ? launch_sweep<float>(a, g.grid, g.threads, g.smem, st)
                                                      : launch_sweep<double>(a, g.grid, g.threads, g.smem, st);
         if (e != cudaSuccess)
@@ -1222,6 +1238,22 @@ bdecon_status bdecon_get_steps(bdecon_handle* h, int32_t p, int32_t c, double* o
     return check_device(h);
 }
 
+bdecon_status bdecon_get_phi(bdecon_handle* h, int32_t p, int32_t c, double* out)
+{
+    if (!h || !out) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    int ci;
+    bdecon_status s = chain_index(h, p, c, &ci);
+    if (s != BDECON_OK) return s;
+    const ProbHost& ph = h->probs[p];
+    const Chain& ch = h->chains[ci];
+    if (!ch.phi) return fail(h, BDECON_ERR_STATE, "not an augmented problem (BDECON_FLAG_AUGMENTED)");
+    const int64_t n = (int64_t)ph.H * ph.W;
+    if (h->precision == BDECON_FP32) launch_convert<float>(ch.phi, h->d_up, n, ph.H, ph.W, ph.pitch, h->st, &h->launches);
+    else launch_convert<double>(ch.phi, h->d_up, n, ph.H, ph.W, ph.pitch, h->st, &h->launches);
+    CK(h, cudaMemcpyAsync(out, h->d_up, 8 * (size_t)n, cudaMemcpyDeviceToHost, h->st));
+    return check_device(h);
+}
+
 bdecon_status bdecon_get_mu(bdecon_handle* h, int32_t p, int32_t c, double* mu)
 {
     if (!h || !mu) return fail(h, BDECON_ERR_INVALID, "bad arguments");
@@ -1297,6 +1329,8 @@ bdecon_status bdecon_delta(bdecon_handle* h, int32_t p, int32_t c, int64_t m, do
     const ProbHost& ph = h->probs[p];
     if (m < 0 || m >= (int64_t)ph.Ho * ph.Wo) return fail(h, BDECON_ERR_INVALID, "pixel %lld out of range", (long long)m);
     if (!(std::isfinite(rho_new) && rho_new > 0.0)) return fail(h, BDECON_ERR_INVALID, "rho_new must be finite and > 0");
+    if (ph.p.flags & BDECON_FLAG_AUGMENTED)
+        return fail(h, BDECON_ERR_STATE, "bdecon_delta evaluates Eq. 6; not available for augmented problems");
     if (h->precision == BDECON_FP32) launch_delta<float>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, h->imgs[p].team, h->st, &h->launches);
     else launch_delta<double>(h->d_imgs + p, h->d_chains + ci, m, rho_new, h->d_out, h->imgs[p].team, h->st, &h->launches);
     CK(h, cudaGetLastError());
@@ -1650,12 +1684,14 @@ bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
         const bdecon_handle* h = ls.hs[ent[e].hi];
         const ProbHost& ph = h->probs[ent[e].pk];
         const int team = h->imgs[ent[e].pk].team;
+        const int aug = ph.p.flags & BDECON_FLAG_AUGMENTED;
         int gi = -1;
         for (size_t q = 0; q < groups.size() && gi < 0; ++q) {
             const Entry& f = ent[groups[q][0]];
             const bdecon_handle* h2 = ls.hs[f.hi];
-            if (S->cfg.one_launch ||
-                (h2->probs[f.pk].L == ph.L && h2->probs[f.pk].S == ph.S && h2->imgs[f.pk].team == team))
+            const ProbHost& ph2 = h2->probs[f.pk];
+            if ((ph2.p.flags & BDECON_FLAG_AUGMENTED) == aug &&
+                (S->cfg.one_launch || (ph2.L == ph.L && ph2.S == ph.S && h2->imgs[f.pk].team == team)))
                 gi = (int)q;
         }
         if (gi < 0) {
@@ -1680,6 +1716,7 @@ bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
     }
     for (auto& gidx : groups) {
         Group g;
+        g.aug = (ls.hs[ent[gidx[0]].hi]->probs[ent[gidx[0]].pk].p.flags & BDECON_FLAG_AUGMENTED) != 0;
         std::vector<PlanItem> items(gidx.size());
         std::vector<PlanItem*> ptrs;
         for (size_t q = 0; q < gidx.size(); ++q) {
@@ -1909,7 +1946,7 @@ bdecon_status bdecon_server_submit(bdecon_server* S, const bdecon_problem* p, in
     j->p.var_map = p->var_map ? j->var.data() : nullptr;
     j->p.psf = j->psf.data();
     j->p.max_sweeps = sweeps;
-    j->p.flags = 0;
+    j->p.flags = p->flags & BDECON_FLAG_AUGMENTED;
     j->sweeps = j->remaining = sweeps;
     size_t bytes = 0;
     st = bdecon_workspace_size(&j->p, 1, &bytes);
