@@ -359,6 +359,29 @@ def run_ours(args):
         e2e = dict(value=upd_per_step / dt, unit="pixel-updates/s", h2d_bytes_per_step=int(h2d),
                    d2h_bytes_per_step=int(d2h), ms_per_step=dt * 1e3)
 
+    # the photon-count augmented float sampler on the same frame (same target)
+    augmented = None
+    if rank == 0 and not args.no_fp64:
+        pa = synth.widefield_512()
+        pa.burn_in = 0
+        pa.refresh_every = S
+        pa.augmented = True
+        sa = bdecon.Sampler(pa, precision=bdecon.BDECON_FP32, max_sweeps=4 * S, stream=stream.cuda_stream)
+        sa.sweep(S)
+        sa.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l2_flush()
+        e0.record(stream)
+        sa.sweep(2 * S)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sa.sync()
+        ta = e0.elapsed_time(e1)
+        acc_a = float(sa.accept_counts()[-2 * S:].sum() / (2 * S * Ho * Wo))
+        sa.close()
+        augmented = dict(value=Ho * Wo * 2 * S / (ta / 1e3), unit="pixel-updates/s", sweeps=2 * S,
+                         ms_per_sweep=ta / (2 * S), acceptance=acc_a)
+
     batched = None
     if rank == 0 and not args.no_batch:
         batched = run_batched(stream.cuda_stream)
@@ -413,6 +436,7 @@ def run_ours(args):
                         "frac": ach_gbs / peaks["hbm_gbs"], "bytes_per_update": alg_bytes_per_update,
                         "peak_source": peaks["source"]},
         "fp64": fp64,
+        "augmented": augmented,
         "batched": batched,
         "serving": serving,
         "acceptance": float(acc[-K * S:].sum() / (K * S * Ho * Wo)),

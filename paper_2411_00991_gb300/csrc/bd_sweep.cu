@@ -22,6 +22,12 @@
 //       the window's expected-image values fetched in one batch
 //   a5  accept iff log u < dL + dP + step z; write rho, mu window, spectrum
 //   a7  after the last class of a sweep: running sums of rho (double)
+// The augmented sampler (AUG, BDECON_FLAG_AUGMENTED) starts every sweep with
+// a photon-count step: each tile draws phi_n ~ p(phi | w_n, mu_n) for the
+// camera pixels centred on its patches (after its neighbours finished the
+// previous sweep), and a3 becomes the Poisson part of the completed
+// likelihood (Eq. 5), sum_n phi_n log(1 + delta K / mu_n) - delta K, with no
+// cumulant cache.
 // In a resident plan the tile's per-pixel data constants (with the PSF halo),
 // patch spectra and object values stay in shared memory for the launch; only
 // mu, shared with the neighbouring tiles, is read from global memory (L2).
