@@ -1633,8 +1633,7 @@ struct bdecon_server {
     std::deque<int64_t> queue;
     std::map<int64_t, SrvJob*> jobs;
     std::vector<SrvJob*> active;        // worker-thread only
-    std::vector<int> job_group;         // per running job: its launch group
-    std::vector<int64_t> job_cost;      // per running job: class steps x rounds per sweep of its blocks
+    std::vector<int64_t> job_cost;      // per running job: class steps x rounds x window pixels per sweep
     size_t mem_used = 0;
     int64_t next_id = 1;
     int64_t segments = 0;
@@ -1744,9 +1743,9 @@ bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
         g.n_chains = (int)ls.gch.size() - g.chain_off;
         ls.groups.push_back(g);
     }
-    // per job: its group and the serial work of one sweep of its blocks
-    // (class steps x patch rounds per team), which sets its sweeps per segment
-    S->job_group.assign(ls.hs.size(), 0);
+    // per job: the serial work of one sweep of its blocks
+    // (class steps x patch rounds per team x window pixels), which sets its
+    // sweeps per segment
     S->job_cost.assign(ls.hs.size(), 1);
     for (size_t gi = 0; gi < ls.groups.size(); ++gi) {
         const Group& g = ls.groups[gi];
@@ -1755,8 +1754,7 @@ bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
             const Image& im = imgs[ch.img];
             const int n_sub = std::max(1, g.threads / im.team);
             const int rounds = (ch.tpi * ch.tpj + n_sub - 1) / n_sub;
-            S->job_group[ls.owner[k]] = (int)gi;
-            S->job_cost[ls.owner[k]] = (int64_t)im.S * im.S * rounds;
+            S->job_cost[ls.owner[k]] = (int64_t)im.S * im.S * rounds * im.L * im.L;
         }
     }
     const size_t bi = sizeof(Image) * imgs.size(), bc = sizeof(Chain) * ls.gch.size();
@@ -1832,17 +1830,16 @@ void srv_loop(bdecon_server* S)
             }
             dirty = false;
         }
-        // sweeps per job in this segment: the slowest job of each launch group
-        // takes segment_sweeps, lighter ones proportionally more (capped by the
-        // slot count, their next refresh and what they have left), so the
-        // group's blocks finish together and small jobs finish early
-        std::vector<int64_t> gmax(ls.groups.size(), 1);
-        for (size_t hi = 0; hi < S->active.size(); ++hi)
-            gmax[S->job_group[hi]] = std::max(gmax[S->job_group[hi]], S->job_cost[hi]);
+        // sweeps per job in this segment: the job with the costliest sweep
+        // takes segment_sweeps, jobs with cheaper sweeps proportionally more
+        // (capped by the slot count, their next refresh and what they have
+        // left), so light jobs finish early instead of with the heaviest
+        int64_t cmax = 1;
+        for (size_t hi = 0; hi < S->active.size(); ++hi) cmax = std::max(cmax, S->job_cost[hi]);
         std::vector<int> lens(S->active.size());
         int len = 1;
         for (size_t hi = 0; hi < S->active.size(); ++hi) {
-            const int64_t want = (int64_t)S->cfg.segment_sweeps * gmax[S->job_group[hi]] / S->job_cost[hi];
+            const int64_t want = (int64_t)S->cfg.segment_sweeps * cmax / S->job_cost[hi];
             lens[hi] = segment_len(S->active[hi]->h, (int)std::min<int64_t>({want, (int64_t)kMaxSlots,
                                                                              (int64_t)S->active[hi]->remaining}));
             len = std::max(len, lens[hi]);

@@ -296,3 +296,11 @@ def test_fp64_exact_chain_with_explicit_team(team_warps):
     prob = synth.small_problem(H=22, W=21, L=11, sigma=1.6, seed=71, maps=True, refresh_every=4, burn_in=2)
     prob.team_warps = team_warps
     _compare_exact(prob, 8)
+
+
+def test_fp64_exact_chain_with_airy_psf():
+    # the paper's widefield PSF shape (pixel-integrated Airy pattern, NA 1.4,
+    # 520 nm, 65 nm pixels) on a 13 x 13 support, sCMOS maps
+    prob = synth.small_problem(H=30, W=26, L=13, maps=True, seed=19, refresh_every=6, burn_in=2)
+    prob.psf = synth.airy_psf(1.4, 520.0, 65.0, 13)
+    _compare_exact(prob, 15)
