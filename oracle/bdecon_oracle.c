@@ -68,6 +68,8 @@ typedef struct {
     double adapt_target; /* > 0: adapt the per-pixel proposal scale during
                             burn-in toward this acceptance rate               */
     int aug;             /* photon-count augmented sampler                     */
+    int sub;             /* object lattice sub cells per camera pixel side (0/1:
+                            the camera grid)                                  */
 } or_problem;
 
 #define OR_ADAPT_GAIN 0.5
@@ -318,10 +320,57 @@ static void normalised_psf(const or_problem* P, double* K)
 
 static int patch_len(int origin, int S, int n) { return (origin + S <= n) ? S : n - origin; }
 
+/* Object lattice f times finer than the camera (f = sub; the paper's
+ * Nyquist lattice, Methods after Eq. 6): camera pixel (a, b) integrates the
+ * f x f lattice cells of its area (the A_n integral of Eq. 1), so
+ *   mu[a][b] = sum_{p,q} Ke[p][q] rho[f a + Le-1-p][f b + Le-1-q]
+ * with the effective kernel Ke = K (x) box_f of side Le = L + f - 1, K the
+ * PSF on the lattice.  The object is (f H + L - 1) x (f W + L - 1).  f = 1
+ * is the camera grid padded by R (Ke = K).                                 */
+static int sub_of(const or_problem* P) { return P->sub > 1 ? P->sub : 1; }
+
+static void obj_dims(const or_problem* P, int* Ho, int* Wo)
+{
+    const int f = sub_of(P);
+    *Ho = f * P->H + P->L - 1;
+    *Wo = f * P->W + P->L - 1;
+}
+
+void or_eff_kernel(const double* K, int L, int f, double* Ke)
+{
+    const int Le = L + f - 1;
+    for (int p = 0; p < Le; ++p)
+        for (int q = 0; q < Le; ++q) {
+            double s = 0.0;
+            for (int u = 0; u < f; ++u)
+                for (int v = 0; v < f; ++v) {
+                    const int pp = p - u, qq = q - v;
+                    if (pp >= 0 && pp < L && qq >= 0 && qq < L) s += K[pp * L + qq];
+                }
+            Ke[p * Le + q] = s;
+        }
+}
+
+/* Eq. 1 on the lattice: the expected image of the camera pixels. */
+void or_expected(const double* rho, int H, int W, const double* Ke, int Le, int f, double* mu)
+{
+    const int Wo = f * (W - 1) + Le;
+    for (int a = 0; a < H; ++a)
+        for (int b = 0; b < W; ++b) {
+            double s = 0.0;
+            for (int p = 0; p < Le; ++p)
+                for (int q = 0; q < Le; ++q)
+                    s += Ke[p * Le + q] * rho[(f * a + Le - 1 - p) * Wo + (f * b + Le - 1 - q)];
+            mu[a * W + b] = s;
+        }
+}
+
 /* Sum of the patch log priors of Eq. 8 over all patches of rho. */
 static double log_prior_all(const or_problem* P, const double* K, const double* rho)
 {
-    const int R = P->L / 2, Ho = P->H + 2 * R, Wo = P->W + 2 * R, S = P->S;
+    int Ho, Wo;
+    obj_dims(P, &Ho, &Wo);
+    const int S = P->S;
     double* re = (double*)malloc((size_t)S * S * sizeof(double));
     double* im = (double*)malloc((size_t)S * S * sizeof(double));
     double* al = (double*)malloc((size_t)S * S * sizeof(double));
@@ -340,16 +389,18 @@ static double log_prior_all(const or_problem* P, const double* K, const double* 
 /* Eq. 9: log posterior (up to the constant log B(alpha) terms) of rho. */
 double or_log_posterior(const or_problem* P, const double* rho)
 {
-    const int H = P->H, W = P->W, L = P->L;
+    const int H = P->H, W = P->W, L = P->L, f = sub_of(P), Le = L + f - 1;
     double* K = (double*)malloc((size_t)L * L * sizeof(double));
+    double* Ke = (double*)malloc((size_t)Le * Le * sizeof(double));
     double* mu = (double*)malloc((size_t)H * W * sizeof(double));
     normalised_psf(P, K);
-    or_convolve(rho, H, W, K, L, mu);
+    or_eff_kernel(K, L, f, Ke);
+    or_expected(rho, H, W, Ke, Le, f, mu);
     double ll = 0.0;
     for (int n = 0; n < H * W; ++n)
         ll += or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu[n]);
     double lp = log_prior_all(P, K, rho);
-    free(K); free(mu);
+    free(K); free(Ke); free(mu);
     return ll + lp;
 }
 
@@ -358,30 +409,35 @@ double or_log_posterior(const or_problem* P, const double* rho)
  * patch log priors.                                                         */
 double or_log_joint(const or_problem* P, const double* rho, const double* phi)
 {
-    const int H = P->H, W = P->W, L = P->L;
+    const int H = P->H, W = P->W, L = P->L, f = sub_of(P), Le = L + f - 1;
     double* K = (double*)malloc((size_t)L * L * sizeof(double));
+    double* Ke = (double*)malloc((size_t)Le * Le * sizeof(double));
     double* mu = (double*)malloc((size_t)H * W * sizeof(double));
     normalised_psf(P, K);
-    or_convolve(rho, H, W, K, L, mu);
+    or_eff_kernel(K, L, f, Ke);
+    or_expected(rho, H, W, Ke, Le, f, mu);
     double ll = 0.0;
     for (int n = 0; n < H * W; ++n)
         ll += or_logjoint_pixel(P->w[n], P->offset[n], P->gain[n], P->var[n], mu[n], (long)phi[n]);
     double lp = log_prior_all(P, K, rho);
-    free(K); free(mu);
+    free(K); free(Ke); free(mu);
     return ll + lp;
 }
 
-/* Initial object: rho0_m = b0 exp(z_m / 10), b0 = max(0.1, mean_n (w_n - o_n) / G_n),
+/* Initial object: rho0_m = b0 exp(z_m / 10), b0 = max(0.1, mean_n (w_n - o_n) / G_n) / f^2,
  * z_m the Box-Muller normal of counter (m, 0, chain, 0) (sweep 0 is never a
  * sampling sweep).  The jitter keeps every patch spectrum coefficient away
  * from zero, where the Dirichlet density of Eq. 7 is singular.           */
 void or_init(const or_problem* P, double* rho)
 {
-    const int R = P->L / 2, Ho = P->H + 2 * R, Wo = P->W + 2 * R;
+    int Ho, Wo;
+    obj_dims(P, &Ho, &Wo);
+    const int f = sub_of(P);
     double mc = 0.0;
     for (int n = 0; n < P->H * P->W; ++n) mc += (P->w[n] - P->offset[n]) / P->gain[n];
     mc /= (double)(P->H * P->W);
-    double b0 = mc > 0.1 ? mc : 0.1;
+    /* a camera pixel collects f^2 lattice cells */
+    double b0 = (mc > 0.1 ? mc : 0.1) / (double)(f * f);
     for (int m = 0; m < Ho * Wo; ++m) {
         double z, u;
         or_draw(P->seed, (uint32_t)m, 0u, (uint32_t)P->chain, &z, &u);
@@ -393,7 +449,10 @@ void or_init(const or_problem* P, double* rho)
 typedef struct {
     const or_problem* P;
     int R, Ho, Wo, S, npi, npj;
+    int f, Le, Lc;    /* lattice cells per camera pixel side, effective
+                         kernel side, camera window side                   */
     double* K;        /* normalised PSF                                   */
+    double* Ke;       /* effective kernel K (x) box_f, Le*Le              */
     double* rho;      /* object, Ho*Wo                                    */
     double* mu;       /* expected image, H*W (kept incrementally)         */
     double** sre;     /* per patch spectrum (ph*pw)                       */
@@ -408,7 +467,7 @@ typedef struct {
 static void cs_refresh(chain_state* c)
 {
     const or_problem* P = c->P;
-    or_convolve(c->rho, P->H, P->W, c->K, P->L, c->mu);
+    or_expected(c->rho, P->H, P->W, c->Ke, c->Le, c->f, c->mu);
     for (int pi = 0; pi < c->npi; ++pi)
         for (int pj = 0; pj < c->npj; ++pj) {
             int i0 = pi * c->S, j0 = pj * c->S;
@@ -422,13 +481,17 @@ static void cs_open(chain_state* c, const or_problem* P, const double* rho_in)
 {
     c->P = P;
     c->R = P->L / 2;
-    c->Ho = P->H + 2 * c->R;
-    c->Wo = P->W + 2 * c->R;
+    obj_dims(P, &c->Ho, &c->Wo);
+    c->f = sub_of(P);
+    c->Le = P->L + c->f - 1;
+    c->Lc = (c->Le - 1) / c->f + 1;
     c->S = P->S;
     c->npi = (c->Ho + c->S - 1) / c->S;
     c->npj = (c->Wo + c->S - 1) / c->S;
     c->K = (double*)malloc((size_t)P->L * P->L * sizeof(double));
     normalised_psf(P, c->K);
+    c->Ke = (double*)malloc((size_t)c->Le * c->Le * sizeof(double));
+    or_eff_kernel(c->K, P->L, c->f, c->Ke);
     c->rho = (double*)malloc((size_t)c->Ho * c->Wo * sizeof(double));
     if (rho_in) memcpy(c->rho, rho_in, (size_t)c->Ho * c->Wo * sizeof(double));
     else or_init(P, c->rho);
@@ -459,7 +522,7 @@ static void cs_close(chain_state* c)
     int np = c->npi * c->npj;
     for (int p = 0; p < np; ++p) { free(c->sre[p]); free(c->sim[p]); free(c->alpha[p]); }
     free(c->sre); free(c->sim); free(c->alpha);
-    free(c->K); free(c->rho); free(c->mu); free(c->tre); free(c->tim); free(c->steps); free(c->phi);
+    free(c->K); free(c->Ke); free(c->rho); free(c->mu); free(c->tre); free(c->tim); free(c->steps); free(c->phi);
 }
 
 /* Likelihood and prior changes for replacing rho_m (m = (i, j)) by rho_new
@@ -469,19 +532,22 @@ static void cs_close(chain_state* c)
 static int cs_delta(chain_state* c, int i, int j, double rho_new, double* dL, double* dP)
 {
     const or_problem* P = c->P;
-    const int R = c->R, L = P->L, H = P->H, W = P->W, S = c->S;
+    const int H = P->H, W = P->W, S = c->S, f = c->f, Le = c->Le, Lc = c->Lc;
     const double delta = rho_new - c->rho[i * c->Wo + j];
     int ok = 1;
     /* Eq. 6 summed over the camera pixels that see object pixel (i, j):
-     * rows a in [i-2R, i], columns b in [j-2R, j], weight K[a-i+2R][b-j+2R]. */
+     * rows a with 0 <= p = f a + Le-1-i < Le (a in [i/f - Lc + 1, i/f]), the
+     * same for columns, weight Ke[p][q] (f = 1: a in [i-2R, i], K[a-i+2R]). */
     double l = 0.0;
-    for (int a = i - 2 * R; a <= i; ++a) {
-        if (a < 0 || a >= H) continue;
-        for (int b = j - 2 * R; b <= j; ++b) {
-            if (b < 0 || b >= W) continue;
+    for (int a = i / f - (Lc - 1); a <= i / f; ++a) {
+        const int p = f * a + Le - 1 - i;
+        if (a < 0 || a >= H || p < 0 || p >= Le) continue;
+        for (int b = j / f - (Lc - 1); b <= j / f; ++b) {
+            const int q = f * b + Le - 1 - j;
+            if (b < 0 || b >= W || q < 0 || q >= Le) continue;
             int n = a * W + b;
             double mu_old = c->mu[n];
-            double mu_new = mu_old + delta * c->K[(a - i + 2 * R) * L + (b - j + 2 * R)];
+            double mu_new = mu_old + delta * c->Ke[p * Le + q];
             if (!(mu_new > 0.0)) { ok = 0; continue; }
             if (P->aug)   /* completed likelihood: the phi-dependent Poisson part */
                 l += c->phi[n] * (log(mu_new) - log(mu_old)) - (mu_new - mu_old);
@@ -515,13 +581,15 @@ static int cs_delta(chain_state* c, int i, int j, double rho_new, double* dL, do
 static void cs_accept(chain_state* c, int i, int j, double rho_new)
 {
     const or_problem* P = c->P;
-    const int R = c->R, L = P->L, H = P->H, W = P->W, S = c->S;
+    const int H = P->H, W = P->W, S = c->S, f = c->f, Le = c->Le, Lc = c->Lc;
     const double delta = rho_new - c->rho[i * c->Wo + j];
-    for (int a = i - 2 * R; a <= i; ++a) {
-        if (a < 0 || a >= H) continue;
-        for (int b = j - 2 * R; b <= j; ++b) {
-            if (b < 0 || b >= W) continue;
-            c->mu[a * W + b] += delta * c->K[(a - i + 2 * R) * L + (b - j + 2 * R)];
+    for (int a = i / f - (Lc - 1); a <= i / f; ++a) {
+        const int p = f * a + Le - 1 - i;
+        if (a < 0 || a >= H || p < 0 || p >= Le) continue;
+        for (int b = j / f - (Lc - 1); b <= j / f; ++b) {
+            const int q = f * b + Le - 1 - j;
+            if (b < 0 || b >= W || q < 0 || q >= Le) continue;
+            c->mu[a * W + b] += delta * c->Ke[p * Le + q];
         }
     }
     int pi = i / S, pj = j / S;
@@ -554,27 +622,32 @@ int or_delta(const or_problem* P, const double* rho, int m, double rho_new, doub
 int or_single_update(const or_problem* P, const double* rho, int m, int t, int* accept,
                      double* rho_new, double* dL, double* dP)
 {
-    const int H = P->H, W = P->W, L = P->L, R = L / 2, S = P->S;
-    const int Ho = H + 2 * R, Wo = W + 2 * R;
+    const int H = P->H, W = P->W, L = P->L, S = P->S, f = sub_of(P), Le = L + f - 1, Lc = (Le - 1) / f + 1;
+    int Ho, Wo;
+    obj_dims(P, &Ho, &Wo);
     const int i = m / Wo, j = m % Wo;
     double* K = (double*)malloc((size_t)L * L * sizeof(double));
+    double* Ke = (double*)malloc((size_t)Le * Le * sizeof(double));
     normalised_psf(P, K);
+    or_eff_kernel(K, L, f, Ke);
     double z, u;
     or_draw(P->seed, (uint32_t)m, (uint32_t)t, (uint32_t)P->chain, &z, &u);
     const double rn = rho[m] * exp(P->step * z);
     const double delta = rn - rho[m];
     int ok = 1;
     double l = 0.0;
-    for (int a = i - 2 * R; a <= i; ++a) {
-        if (a < 0 || a >= H) continue;
-        for (int b = j - 2 * R; b <= j; ++b) {
-            if (b < 0 || b >= W) continue;
+    for (int a = i / f - (Lc - 1); a <= i / f; ++a) {
+        const int pa = f * a + Le - 1 - i;
+        if (a < 0 || a >= H || pa < 0 || pa >= Le) continue;
+        for (int b = j / f - (Lc - 1); b <= j / f; ++b) {
+            const int qb = f * b + Le - 1 - j;
+            if (b < 0 || b >= W || qb < 0 || qb >= Le) continue;
             double mu = 0.0;
-            for (int p = 0; p < L; ++p)
-                for (int q = 0; q < L; ++q)
-                    mu += K[p * L + q] * rho[(a + 2 * R - p) * Wo + (b + 2 * R - q)];
+            for (int p = 0; p < Le; ++p)
+                for (int q = 0; q < Le; ++q)
+                    mu += Ke[p * Le + q] * rho[(f * a + Le - 1 - p) * Wo + (f * b + Le - 1 - q)];
             const int n = a * W + b;
-            const double mu_new = mu + delta * K[(a - i + 2 * R) * L + (b - j + 2 * R)];
+            const double mu_new = mu + delta * Ke[pa * Le + qb];
             if (!(mu_new > 0.0)) { ok = 0; continue; }
             l += or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu_new)
                - or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu);
@@ -601,7 +674,7 @@ int or_single_update(const or_problem* P, const double* rho, int m, int t, int* 
     *rho_new = rn;
     *dL = ok ? l : 0.0;
     *dP = pr;
-    free(K); free(re); free(im); free(re2); free(im2); free(al); free(x);
+    free(K); free(Ke); free(re); free(im); free(re2); free(im2); free(al); free(x);
     return ok;
 }
 

@@ -40,7 +40,7 @@ class OrProblem(C.Structure):
                 ("var", C.c_void_p), ("psf", C.c_void_p),
                 ("seed", C.c_uint64), ("chain", C.c_int), ("step", C.c_double),
                 ("burn_in", C.c_int), ("refresh_every", C.c_int), ("adapt_target", C.c_double),
-                ("aug", C.c_int)]
+                ("aug", C.c_int), ("sub", C.c_int)]
 
 
 def lib():
@@ -62,6 +62,10 @@ def lib():
         L.or_log_prior_patch.restype = C.c_double
         L.or_log_posterior.argtypes = [C.POINTER(OrProblem), C.c_void_p]
         L.or_log_posterior.restype = C.c_double
+        L.or_eff_kernel.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+        L.or_eff_kernel.restype = None
+        L.or_expected.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+        L.or_expected.restype = None
         L.or_log_joint.argtypes = [C.POINTER(OrProblem), C.c_void_p, C.c_void_p]
         L.or_log_joint.restype = C.c_double
         L.or_sample_phi.argtypes = [C.c_double] * 6
@@ -108,6 +112,19 @@ def draw(seed: int, m: int, t: int, chain: int):
     z, u = C.c_double(), C.c_double()
     lib().or_draw(int(seed), int(m), int(t), int(chain), C.byref(z), C.byref(u))
     return z.value, u.value
+
+
+def expected(rho, H, W, K, f) -> np.ndarray:
+    """Eq. 1 on a lattice f times finer than the camera (oracle)."""
+    K = np.ascontiguousarray(K, dtype=np.float64)
+    L = K.shape[0]
+    Le = L + f - 1
+    Ke = np.empty((Le, Le))
+    lib().or_eff_kernel(_p(K), L, int(f), _p(Ke))
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    mu = np.empty((H, W))
+    lib().or_expected(_p(rho), int(H), int(W), _p(Ke), Le, int(f), _p(mu))
+    return mu
 
 
 def sample_phi(w, o, G, var, mu, u) -> int:
@@ -176,7 +193,7 @@ class Oracle:
         self.c = OrProblem(prob.H, prob.W, prob.L, prob.S, _p(self.w), _p(self.g), _p(self.o),
                            _p(self.v), _p(self.psf), int(prob.seed), int(chain), float(prob.step),
                            int(prob.burn_in), int(prob.refresh_every), float(getattr(prob, "adapt_target", 0.0)),
-                           int(bool(getattr(prob, "augmented", False))))
+                           int(bool(getattr(prob, "augmented", False))), int(getattr(prob, "subpixel", 1)))
         self.Ho, self.Wo = prob.object_shape()
 
     def log_joint(self, rho: np.ndarray, phi: np.ndarray) -> float:

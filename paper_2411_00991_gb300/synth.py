@@ -50,6 +50,7 @@ class Problem:
     n_samples: int = 0           # kept objects per chain (0 -> none)
     adapt_target: float = 0.0    # > 0: adapt each pixel's proposal scale during burn-in toward this acceptance
     augmented: bool = False      # photon-count augmented sampler (completed likelihood, Eq. 5)
+    subpixel: int = 1            # object lattice cells per camera pixel side (psf given on that lattice)
 
     @property
     def H(self) -> int:
@@ -69,7 +70,8 @@ class Problem:
 
     @property
     def S(self) -> int:
-        return self.stride if self.stride else self.L
+        # the default stride covers the camera window of one update (L + f - 1)
+        return self.stride if self.stride else self.L + max(1, int(self.subpixel)) - 1
 
     def maps(self):
         """(gain, offset, var) expanded to float64 (H, W) maps."""
@@ -82,7 +84,8 @@ class Problem:
         return tuple(out)
 
     def object_shape(self):
-        return (self.H + 2 * self.R, self.W + 2 * self.R)
+        f = max(1, int(self.subpixel))
+        return (f * self.H + 2 * self.R, f * self.W + 2 * self.R)
 
 
 # ---------------------------------------------------------------- PSF ----
@@ -183,13 +186,24 @@ def _scale(struct, peak, background):
 
 # -------------------------------------------------------------- camera ----
 
-def simulate_frame(truth: np.ndarray, psf: np.ndarray, gain, offset, var,
-                   rng: np.random.Generator) -> np.ndarray:
-    """Camera frame from the object (Eq. 1-4): valid blur of the padded object,
-    Poisson photons, gain and offset, Gaussian read noise; float32 ADU, not
-    rounded."""
+def expected_image(truth: np.ndarray, psf: np.ndarray, subpixel: int = 1) -> np.ndarray:
+    """Eq. 1 for the generator: valid blur of the padded object on its lattice,
+    then the f x f lattice cells of each camera pixel summed (f = subpixel)."""
     from scipy.signal import fftconvolve
-    mu = fftconvolve(truth, psf, mode="valid")
+    fine = fftconvolve(truth, psf, mode="valid")
+    f = max(1, int(subpixel))
+    if f == 1:
+        return fine
+    H, W = fine.shape[0] // f, fine.shape[1] // f
+    return fine[:H * f, :W * f].reshape(H, f, W, f).sum(axis=(1, 3))
+
+
+def simulate_frame(truth: np.ndarray, psf: np.ndarray, gain, offset, var,
+                   rng: np.random.Generator, subpixel: int = 1) -> np.ndarray:
+    """Camera frame from the object (Eq. 1-4): valid blur of the padded object,
+    binned to camera pixels, Poisson photons, gain and offset, Gaussian read
+    noise; float32 ADU, not rounded."""
+    mu = expected_image(truth, psf, subpixel)
     mu = np.maximum(mu, 0.0)
     phot = rng.poisson(mu).astype(np.float64)
     g = np.asarray(gain, dtype=np.float64)
@@ -211,24 +225,28 @@ def scmos_maps(H, W, rng, offset_mean=100.0, offset_sd=2.0, var_shape=2.0, var_s
 
 def small_problem(H=20, W=24, L=5, sigma=1.0, peak=20.0, background=2.0,
                   seed=7, maps=False, stride=0, n_chains=1, refresh_every=7,
-                  burn_in=0, step=0.2) -> Problem:
+                  burn_in=0, step=0.2, subpixel=1) -> Problem:
     """A few-tile problem for parity tests (ragged patch tail when the padded
-    size is not a multiple of the stride)."""
+    size is not a multiple of the stride).  With subpixel = f the object lives
+    on a lattice f times finer than the camera (PSF side L and sigma in
+    lattice units), the photon levels per camera pixel unchanged."""
     rng = np.random.default_rng(seed)
     R = L // 2
-    shape = (H + 2 * R, W + 2 * R)
-    struct = _blobs(shape, max(2, H * W // 120), 1.0, 2.5, 0.3, 1.0, rng) + _lines(shape, 2, rng)
-    truth = _scale(struct, peak, background)
+    f = max(1, int(subpixel))
+    shape = (f * H + 2 * R, f * W + 2 * R)
+    struct = _blobs(shape, max(2, H * W // 120), 1.0 * f, 2.5 * f, 0.3, 1.0, rng) + _lines(shape, 2, rng)
+    truth = _scale(struct, peak, background) / (f * f)
     psf = gaussian_psf(sigma, L)
     if maps:
         off, var = scmos_maps(H, W, rng)
         gain = 2.1
     else:
         off, var, gain = 100.0, 2.56, 2.0
-    img = simulate_frame(truth, psf, gain, off, var, rng)
+    img = simulate_frame(truth, psf, gain, off, var, rng, subpixel=f)
     return Problem(image=img, psf=psf, gain=gain, offset=off, var=var, stride=stride,
                    n_chains=n_chains, seed=seed, step=step, burn_in=burn_in,
-                   refresh_every=refresh_every, truth=truth, name=f"small{H}x{W}L{L}")
+                   refresh_every=refresh_every, truth=truth, name=f"small{H}x{W}L{L}f{f}",
+                   subpixel=f)
 
 
 def widefield_64(seed=0) -> Problem:
