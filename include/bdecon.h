@@ -79,9 +79,9 @@ typedef struct {
     double offset;
     const float* var_map;      /* H*W read-noise variance (ADU^2) or NULL -> read_var */
     double read_var;
-    int32_t stride;            /* sub-lattice stride = prior patch side S; 0 -> L;
-                                  must be >= L.  Part of the model (it sets the
-                                  prior's patches).                                 */
+    int32_t stride;            /* sub-lattice stride = prior patch side S; 0 -> L
+                                  (L + f - 1 with subpixel f); must be >= that.  Part
+                                  of the model (it sets the prior's patches).       */
     int32_t n_chains;          /* independent chains, >= 1                          */
     uint64_t seed;             /* Philox key                                        */
     double step;               /* sd of the log-space random walk; 0 -> 0.2         */
@@ -111,6 +111,15 @@ typedef struct {
                                   s_m *= exp(g (1 - adapt_target)) if accepted,
                                   exp(-g adapt_target) if not, g = 0.5/sqrt(t),
                                   clamped to [1e-4, 4]; fixed after burn-in      */
+    int32_t subpixel;          /* object lattice cells per camera pixel side f, 0..8
+                                  (0 -> 1: the camera grid).  With f > 1 the object
+                                  lives on a lattice f times finer (the paper's
+                                  Nyquist lattice); psf is given on that lattice and
+                                  each camera pixel sums its f x f cells (Eq. 1):
+                                  mu[a][b] = sum Ke[p][q] rho[f a+Le-1-p][f b+Le-1-q],
+                                  Ke = psf (x) box_f of side Le = L + f - 1.  The
+                                  object is (f H + L - 1) x (f W + L - 1); stride
+                                  defaults to Le and must be >= Le.                */
 } bdecon_problem;
 
 #define BDECON_FLAG_ACCEPT_LOG 1   /* keep the accept decision of every update of

@@ -47,7 +47,7 @@ class _Problem(C.Structure):
                 ("step", C.c_double), ("burn_in", C.c_int32), ("refresh_every", C.c_int32),
                 ("precision", C.c_int32), ("max_sweeps", C.c_int32), ("flags", C.c_int32),
                 ("team_warps", C.c_int32), ("sample_every", C.c_int32), ("n_samples", C.c_int32),
-                ("adapt_target", C.c_double)]
+                ("adapt_target", C.c_double), ("subpixel", C.c_int32)]
 
 
 EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bdecon_create_in",
@@ -165,7 +165,8 @@ def _problem(pr, precision, max_sweeps, flags, keep) -> _Problem:
                     int(pr.burn_in), int(pr.refresh_every), int(precision), int(max_sweeps),
                     int(flags) | (FLAG_AUGMENTED if getattr(pr, "augmented", False) else 0),
                     int(getattr(pr, "team_warps", 0)), int(getattr(pr, "sample_every", 0)),
-                    int(getattr(pr, "n_samples", 0)), float(getattr(pr, "adapt_target", 0.0)))
+                    int(getattr(pr, "n_samples", 0)), float(getattr(pr, "adapt_target", 0.0)),
+                    int(getattr(pr, "subpixel", 1)))
 
 
 def log_posterior_static(H, W, image_ptr, L, psf_ptr, gain, offset, var, stride, rho_ptr, out_ptr,
@@ -253,10 +254,13 @@ class Sampler:
             pass
 
     def _shape(self, p):
+        """(crop rows, crop cols, object rows, object cols) of problem p: the
+        crop is the object area under the camera, f H x f W for subpixel f."""
         pr = self.problems[p]
         H, W = np.asarray(pr.image).shape
         R = np.asarray(pr.psf).shape[0] // 2
-        return H, W, H + 2 * R, W + 2 * R
+        f = max(1, int(getattr(pr, "subpixel", 1)))
+        return f * H, f * W, f * H + 2 * R, f * W + 2 * R
 
     # ----------------------------------------------------------- sampling --
     def sweep(self, n: int):
@@ -341,8 +345,8 @@ class Sampler:
         self._ck(self.L.bdecon_set_state(self.h, p, c, _p(rho), int(sweeps)))
 
     def get_phi(self, p: int = 0, c: int = 0) -> np.ndarray:
-        """Photon counts of an augmented chain, (H, W)."""
-        H, W, Ho, Wo = self._shape(p)
+        """Photon counts of an augmented chain, (H, W) camera pixels."""
+        H, W = np.asarray(self.problems[p].image).shape
         out = np.empty((H, W))
         self._ck(self.L.bdecon_get_phi(self.h, p, c, _p(out)))
         return out
@@ -355,7 +359,8 @@ class Sampler:
         return out
 
     def get_mu(self, p: int = 0, c: int = 0) -> np.ndarray:
-        H, W, Ho, Wo = self._shape(p)
+        """Expected image of chain c, (H, W) camera pixels."""
+        H, W = np.asarray(self.problems[p].image).shape
         mu = np.empty((H, W))
         self._ck(self.L.bdecon_get_mu(self.h, p, c, _p(mu)))
         return mu

@@ -93,8 +93,8 @@ template <> struct Vec2<double> { using type = double2; };
 template <typename T> struct alignas(4 * sizeof(T)) Dat4 { T c, is2, beta, lnorm; };
 
 template <typename T> __device__ __forceinline__ const T* kern(const Image& im);
-template <> __device__ __forceinline__ const float* kern<float>(const Image& im) { return im.K32; }
-template <> __device__ __forceinline__ const double* kern<double>(const Image& im) { return im.K64; }
+template <> __device__ __forceinline__ const float* kern<float>(const Image& im) { return im.Ke32; }
+template <> __device__ __forceinline__ const double* kern<double>(const Image& im) { return im.Ke64; }
 template <typename T> __device__ __forceinline__ const Dat4<T>* dat(const Image& im);
 template <> __device__ __forceinline__ const Dat4<float>* dat<float>(const Image& im)
 {

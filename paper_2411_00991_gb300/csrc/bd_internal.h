@@ -53,6 +53,10 @@ struct Image {
     int64_t spec_len;                // complex elements per chain
     int n_ent, n_tw, max_nhalf;      // table sizes (all shapes)
     int team;                        // threads per pixel update (a property of the problem)
+    int f, Le, Lc;                   // object cells per camera pixel side, effective kernel side L + f - 1,
+                                     // camera window side (Le - 1) / f + 1 (f = 1: L, L)
+    const double* Ke64;              // Le*Le effective kernel K (x) box_f (f = 1: the PSF itself)
+    const float* Ke32;
     int sample_every, n_samples;     // kept objects: every sample_every-th sweep past burn-in, n_samples slots
     const double* adapt_fac;         // [burn_in][2] proposal-scale factors after accept / reject, or null
 };
@@ -88,6 +92,7 @@ struct SweepArgs {
     int n_chains;
     int n_sweeps;                    // sweeps in this launch (chains may take fewer)
     int aug;                         // photon-count augmented sampler (every chain of the launch)
+    int fine;                        // object lattices finer than the camera (every chain of the launch)
     int* err;
     int resident;                    // 1: tile state (data, spectra, rho) held in shared memory
     unsigned long long wait_ns;      // limit of each neighbour wait
@@ -124,22 +129,26 @@ __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15
 struct SmemPlan {
     size_t red, K, tw, ekl, ewa, em, spec, rho, dat, total;
 };
-__host__ __device__ inline SmemPlan smem_plan(int L, int S, int n_tw, int n_ent, int max_nhalf, int tpi, int tpj,
-                                              int resident, int tsize)
+__host__ __device__ inline SmemPlan smem_plan(int L, int f, int S, int n_tw, int n_ent, int max_nhalf, int tpi,
+                                              int tpj, int resident, int tsize)
 {
     SmemPlan p;
     size_t o = 0;
+    const int Le = L + f - 1, Lc = (Le - 1) / f + 1;
     p.red = o; o += al16((size_t)2 * 8 * 8 * 4 * tsize);
-    p.K = o; o += al16((size_t)L * L * tsize);
+    p.K = o; o += al16((size_t)Le * Le * tsize);
     p.tw = o; o += al16((size_t)2 * n_tw * tsize);
     p.ekl = o; o += al16((size_t)4 * n_ent);
     p.ewa = o; o += al16((size_t)n_ent * tsize);
     p.em = o; o += al16((size_t)n_ent * tsize);
     if (resident) {
         const int R = L / 2;
+        // camera rows / columns seen by the tile's windows
+        const int ch = f == 1 ? tpi * S + 2 * R : (tpi * S + f - 1) / f + Lc;
+        const int cw = f == 1 ? tpj * S + 2 * R : (tpj * S + f - 1) / f + Lc;
         p.spec = o; o += al16((size_t)tpi * tpj * max_nhalf * 2 * tsize);
         p.rho = o; o += al16((size_t)tpi * tpj * S * S * tsize);
-        p.dat = o; o += al16((size_t)(tpi * S + 2 * R) * (tpj * S + 2 * R) * 4 * tsize);
+        p.dat = o; o += al16((size_t)ch * cw * 4 * tsize);
     } else {
         p.spec = p.rho = p.dat = o;
     }
@@ -169,7 +178,7 @@ void launch_sample_phi(const Image& im, const Chain& ch, int t, int* err, cudaSt
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 template <typename T>
-int sweep_blocks_per_sm(int threads, size_t smem, bool aug);
+int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine);
 // zero every chain's progress words, last-accept words and trace partials
 void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_slots, cudaStream_t st,
                   int64_t* launches);

@@ -44,6 +44,25 @@ __global__ void __launch_bounds__(kRedThreads) k_setup_psf(int L, const double* 
     }
 }
 
+// Effective kernel of a lattice f times finer than the camera: a camera
+// pixel sums the f x f cells of its area (the pixel integral of Eq. 1), so
+// Ke[p][q] = sum_{u,v < f} K[p-u][q-v], side Le = L + f - 1.
+__global__ void k_setup_eff(int L, int f, const double* K64, double* Ke64, float* Ke32)
+{
+    const int Le = L + f - 1;
+    for (int idx = threadIdx.x; idx < Le * Le; idx += blockDim.x) {
+        const int p = idx / Le, q = idx % Le;
+        double s = 0.0;
+        for (int u = 0; u < f; ++u)
+            for (int v = 0; v < f; ++v) {
+                const int pp = p - u, qq = q - v;
+                if (pp >= 0 && pp < L && qq >= 0 && qq < L) s += K64[pp * L + qq];
+            }
+        Ke64[idx] = s;
+        Ke32[idx] = (float)s;
+    }
+}
+
 // c = (w - o)/G, s^2 = var/G^2 (photon units), 1/s^2, exp(-1/s^2), -log(2 pi var)/2
 __global__ void __launch_bounds__(kRedThreads) k_setup_data(int n, const float* w, const float* g, const float* o,
                                                            const float* v, double gs, double os, double vs,
@@ -74,7 +93,7 @@ __global__ void __launch_bounds__(kRedThreads) k_setup_data(int n, const float* 
 }
 
 // b0 = max(0.1, mean_n c_n)
-__global__ void __launch_bounds__(kRedThreads) k_setup_b0(const double* part_c, int nblk, int npix, double* b0)
+__global__ void __launch_bounds__(kRedThreads) k_setup_b0(const double* part_c, int nblk, int npix, int f, double* b0)
 {
     __shared__ double sh[kRedThreads];
     double s = 0.0;
@@ -82,7 +101,7 @@ __global__ void __launch_bounds__(kRedThreads) k_setup_b0(const double* part_c, 
     const double tot = block_sum(s, sh);
     if (threadIdx.x == 0) {
         const double m = tot / (double)npix;
-        b0[0] = m > 0.1 ? m : 0.1;
+        b0[0] = (m > 0.1 ? m : 0.1) / (double)(f * f);   // a camera pixel collects f^2 cells
     }
 }
 
@@ -167,12 +186,16 @@ void launch_setup(const Image& im, const Image* d_im, const float* w, const floa
 {
     (void)d_im;
     k_setup_psf<<<1, kRedThreads, 0, st>>>(im.L, psf_raw, const_cast<double*>(im.K64), const_cast<float*>(im.K32));
+    if (im.f > 1) {
+        k_setup_eff<<<1, 256, 0, st>>>(im.L, im.f, im.K64, const_cast<double*>(im.Ke64), const_cast<float*>(im.Ke32));
+        ++*launches;
+    }
     const int npix = im.H * im.W;
     const int nblk = (npix + kRedThreads - 1) / kRedThreads;
     double* part_c = scratch;                       // nblk
     k_setup_data<<<nblk, kRedThreads, 0, st>>>(npix, w, g, o, v, gs, os, vs, const_cast<double*>(im.dat64),
                                                const_cast<float*>(im.dat32), part_c);
-    k_setup_b0<<<1, kRedThreads, 0, st>>>(part_c, nblk, npix, b0_out);
+    k_setup_b0<<<1, kRedThreads, 0, st>>>(part_c, nblk, npix, im.f, b0_out);
     *launches += 3;
     // twiddles: the distinct patch sides appear at the shapes' offsets
     for (int s = 0; s < kMaxShapes; ++s) {
@@ -215,11 +238,12 @@ __global__ void __launch_bounds__(kRedThreads) k_refresh_mu(Image im, Chain ch, 
     if (idx < im.H * im.W) {
         const int a = idx / im.W, b = idx % im.W;
         const T* rho = reinterpret_cast<const T*>(ch.rho);
-        const int L = im.L, R = im.R;
+        // Eq. 1 on the object lattice: mu[a][b] = sum Ke[p][q] rho[f a + Le-1-p][f b + Le-1-q]
+        const int Le = im.Le, f = im.f;
         double mu = 0.0;
-        for (int p = 0; p < L; ++p) {
-            const T* row = rho + (size_t)(a + 2 * R - p) * im.Wo + (b + 2 * R);
-            for (int q = 0; q < L; ++q) mu += im.K64[p * L + q] * (double)row[-q];
+        for (int p = 0; p < Le; ++p) {
+            const T* row = rho + (size_t)(f * a + Le - 1 - p) * im.Wo + (f * b + Le - 1);
+            for (int q = 0; q < Le; ++q) mu += im.Ke64[p * Le + q] * (double)row[-q];
         }
         if (!(mu > 0.0) || !isfinite(mu)) {
             atomicOr(err, kErrNumeric);

@@ -80,6 +80,31 @@ __device__ __forceinline__ void twiddle(const T* tw, const Shape& sh, int kl, in
 
 constexpr int kMaxPx = 4;   // window pixels per thread fetched in one batch
 
+// Window cell k (0 <= k < Lc^2) of object pixel (i, j): the camera pixel
+// (aa, bb) it weighs on and the entry kw of the effective kernel Ke (Le x Le)
+// with mu[aa][bb] = sum Ke[p][q] rho[f aa + Le-1-p][f bb + Le-1-q].  False
+// when the cell is outside the frame (or, for f > 1, outside the kernel at
+// this sub-cell phase).  f = 1 (FINE false): aa = i - 2R + k / L, kw = k.
+template <bool FINE>
+__device__ __forceinline__ bool win_cell(const Image& im, int i, int j, int k, int& aa, int& bb, int& kw)
+{
+    if (!FINE) {
+        const int L = im.L, R = im.R;
+        aa = i - 2 * R + k / L;
+        bb = j - 2 * R + (k - (k / L) * L);
+        kw = k;
+        return k < L * L && (unsigned)aa < (unsigned)im.H && (unsigned)bb < (unsigned)im.W;
+    }
+    const int f = im.f, Le = im.Le, Lc = im.Lc;
+    const int kr = k / Lc, kc = k - kr * Lc;
+    aa = i / f - (Lc - 1) + kr;
+    bb = j / f - (Lc - 1) + kc;
+    const int p = f * aa + Le - 1 - i, q = f * bb + Le - 1 - j;
+    kw = p * Le + q;
+    return k < Lc * Lc && (unsigned)aa < (unsigned)im.H && (unsigned)bb < (unsigned)im.W && (unsigned)p < (unsigned)Le &&
+           (unsigned)q < (unsigned)Le;
+}
+
 // a2: the proposal of one update from its Philox counter (m, t, chain, 0):
 // z standard normal (Box-Muller), log u, the log-space move hz = s_m z (s_m
 // the pixel's scale: its adapted one, else the problem's step) and
@@ -105,17 +130,17 @@ __device__ __forceinline__ void proposal(const Image& im, const Chain& ch, int m
 // and bad flag in out[0..1].  muv keeps the fetched expected image values.
 // Fetch the first batch of a thread's window values (expected image and
 // cached cumulants) so the loads are in flight while other work proceeds.
-template <typename T, bool CUM>
+template <typename T, bool CUM, bool FINE>
 __device__ __forceinline__ void window_fetch(const T* mu_g, const float4* cum_g, const float2* cum2_g,
                                              const Image& im, int i, int j, int lt, T (&muv)[kMaxPx],
                                              float4 (&cq)[kMaxPx], float2 (&cq2)[kMaxPx], int k0)
 {
-    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L, NT = im.team;
+    const int NT = im.team;
 #pragma unroll
     for (int jj = 0; jj < kMaxPx; ++jj) {
         const int k = k0 + jj * NT;
-        const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
-        const bool in = k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W;
+        int aa, bb, kw;
+        const bool in = win_cell<FINE>(im, i, j, k, aa, bb, kw);
         muv[jj] = in ? __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb) : (T)-1;
         if (CUM) {
             cq[jj] = in ? __ldcg(cum_g + (size_t)aa * im.mu_pitch + bb) : make_float4(0, 0, 0, 0);
@@ -124,24 +149,24 @@ __device__ __forceinline__ void window_fetch(const T* mu_g, const float4* cum_g,
     }
 }
 
-template <typename T, bool RES, bool CUM>
+template <typename T, bool RES, bool CUM, bool FINE>
 __device__ __forceinline__ void lik_partial(const T* mu_g, const float4* cum_g, const float2* cum2_g, const Dat4<T>* dat_s,
                                             const Dat4<T>* dat_g, const T* Ks, const Image& im, int i, int j,
                                             int a_lo, int b_lo, int rw, int lt, int NT, T delta, T (&muv)[kMaxPx],
                                             T* out, int lane, float4 (&cq)[kMaxPx], float2 (&cq2)[kMaxPx],
                                             bool prefetched)
 {
-    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L;
+    const int W = im.W, LL = FINE ? im.Lc * im.Lc : im.L * im.L;
     T accL = 0;
     bool badL = false;
     for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
-        if (!(prefetched && k0 == lt)) window_fetch<T, CUM>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, k0);
+        if (!(prefetched && k0 == lt)) window_fetch<T, CUM, FINE>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, k0);
 #pragma unroll
         for (int jj = 0; jj < kMaxPx; ++jj) {
             const int k = k0 + jj * NT;
-            const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
-            if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
-                const T xk = mul_rn(delta, Ks[k]);
+            int aa, bb, kw;
+            if (win_cell<FINE>(im, i, j, k, aa, bb, kw)) {
+                const T xk = mul_rn(delta, Ks[kw]);
                 if (CUM) {
                     const float d = (float)xk * Prec<float>::rcp((float)muv[jj]);
                     if (fabsf(d) <= kCumEval) {
@@ -170,16 +195,16 @@ __device__ __forceinline__ void lik_partial(const T* mu_g, const float4* cum_g, 
 }
 
 // Augmented sampler: the window's expected image and photon counts.
-template <typename T>
+template <typename T, bool FINE>
 __device__ __forceinline__ void window_fetch_aug(const T* mu_g, const T* phi_g, const Image& im, int i, int j,
                                                  T (&muv)[kMaxPx], T (&phv)[kMaxPx], int k0)
 {
-    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L, NT = im.team;
+    const int NT = im.team;
 #pragma unroll
     for (int jj = 0; jj < kMaxPx; ++jj) {
         const int k = k0 + jj * NT;
-        const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
-        const bool in = k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W;
+        int aa, bb, kw;
+        const bool in = win_cell<FINE>(im, i, j, k, aa, bb, kw);
         muv[jj] = in ? __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb) : (T)-1;
         phv[jj] = in ? __ldcg(phi_g + (size_t)aa * im.mu_pitch + bb) : (T)0;
     }
@@ -190,22 +215,22 @@ __device__ __forceinline__ void window_fetch_aug(const T* mu_g, const T* phi_g, 
 //   sum_n phi_n log(1 + delta K/mu_n) - delta K,
 // a proposal making some mu'_n <= 0 being impossible.  Same thread
 // assignment and reduction as lik_partial.
-template <typename T>
+template <typename T, bool FINE>
 __device__ __forceinline__ void lik_partial_aug(const T* mu_g, const T* phi_g, const T* Ks, const Image& im, int i,
                                                 int j, int lt, int NT, T delta, T (&muv)[kMaxPx], T (&phv)[kMaxPx],
                                                 T* out, int lane, bool prefetched)
 {
-    const int L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L;
+    const int LL = FINE ? im.Lc * im.Lc : im.L * im.L;
     T accL = 0;
     bool badL = false;
     for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
-        if (!(prefetched && k0 == lt)) window_fetch_aug<T>(mu_g, phi_g, im, i, j, muv, phv, k0);
+        if (!(prefetched && k0 == lt)) window_fetch_aug<T, FINE>(mu_g, phi_g, im, i, j, muv, phv, k0);
 #pragma unroll
         for (int jj = 0; jj < kMaxPx; ++jj) {
             const int k = k0 + jj * NT;
-            const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
-            if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
-                const T xk = mul_rn(delta, Ks[k]);
+            int aa, bb, kw;
+            if (win_cell<FINE>(im, i, j, k, aa, bb, kw)) {
+                const T xk = mul_rn(delta, Ks[kw]);
                 const T d = xk / muv[jj];
                 if (!(d > (T)-1)) {
                     badL = true;
@@ -226,7 +251,7 @@ __device__ __forceinline__ void lik_partial_aug(const T* mu_g, const T* phi_g, c
     }
 }
 
-template <typename T, bool RES, bool AUG>
+template <typename T, bool RES, bool AUG, bool FINE>
 __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_sweep(SweepArgs a)
 {
     using P = Prec<T>;
@@ -258,16 +283,21 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     const int t0 = *ch.tdev;          // sweeps completed before this launch (advanced after it by k_trace)
     const int tl = (int)blockIdx.x - ch.cta_base;
     const int ti = tl / ch.ntj, tj = tl - (tl / ch.ntj) * ch.ntj;
-    const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W, S2 = S * S, LL = L * L;
+    const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W, S2 = S * S;
+    // lattice f times finer than the camera (FINE; f = 1 otherwise): LL window cells per update
+    const int f = FINE ? im.f : 1, Le = FINE ? im.Le : L, Lc = FINE ? im.Lc : L, LL = Lc * Lc;
     const int pi0 = ti * ch.tpi, pj0 = tj * ch.tpj;
     const int pi1 = min(pi0 + ch.tpi, im.npi), pj1 = min(pj0 + ch.tpj, im.npj);
     const int tw_ = pj1 - pj0, npt = (pi1 - pi0) * tw_;
     // camera region seen by the tile's windows
     const int i0 = pi0 * S, j0 = pj0 * S, i1 = min(pi1 * S, im.Ho), j1 = min(pj1 * S, im.Wo);
-    const int a_lo = max(0, i0 - 2 * R), a_hi = min(H, i1), b_lo = max(0, j0 - 2 * R), b_hi = min(W, j1);
+    const int a_lo = !FINE ? max(0, i0 - 2 * R) : max(0, i0 / f - (Lc - 1));
+    const int a_hi = !FINE ? min(H, i1) : min(H, (i1 - 1) / f + 1);
+    const int b_lo = !FINE ? max(0, j0 - 2 * R) : max(0, j0 / f - (Lc - 1));
+    const int b_hi = !FINE ? min(W, j1) : min(W, (j1 - 1) / f + 1);
     const int rw = b_hi - b_lo;
 
-    const SmemPlan sp = smem_plan(L, S, im.n_tw, im.n_ent, im.max_nhalf, ch.tpi, ch.tpj, RES ? 1 : 0, sizeof(T));
+    const SmemPlan sp = smem_plan(L, f, S, im.n_tw, im.n_ent, im.max_nhalf, ch.tpi, ch.tpj, RES ? 1 : 0, sizeof(T));
     T* red = reinterpret_cast<T*>(smem + sp.red);          // [2][8 sub-teams][8 warps][4]
     T* Ks = reinterpret_cast<T*>(smem + sp.K);
     T* tws = reinterpret_cast<T*>(smem + sp.tw);
@@ -299,7 +329,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         s_stale = 0;
         s_acc_any = 0;
     }
-    for (int k = tid; k < LL; k += blockDim.x) Ks[k] = kern<T>(im)[k];
+    for (int k = tid; k < Le * Le; k += blockDim.x) Ks[k] = kern<T>(im)[k];
     for (int k = tid; k < 2 * im.n_tw; k += blockDim.x) tws[k] = twid<T>(im)[k];
     for (int k = tid; k < im.n_ent; k += blockDim.x) {
         ekl[k] = im.ent_kl[k];
@@ -382,9 +412,13 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                         const Shape& shp = im.shape[shape_index(im, pi, pj)];
                         int bad = 0;
                         for (int e = lt; e < shp.ph * shp.pw; e += NT) {
+                            // the camera pixel anchored at this object pixel: object row
+                            // f a + R (f = 1: every object pixel anchors one)
                             const int uu = e / shp.pw, vv = e - (e / shp.pw) * shp.pw;
-                            const int aa = pi * S + uu - R, bb = pj * S + vv - R;
-                            if ((unsigned)aa >= (unsigned)H || (unsigned)bb >= (unsigned)W) continue;
+                            const int ir = pi * S + uu - R, jr = pj * S + vv - R;
+                            if (ir < 0 || jr < 0 || ir % f != 0 || jr % f != 0) continue;
+                            const int aa = ir / f, bb = jr / f;
+                            if (aa >= H || bb >= W) continue;
                             const size_t idx = (size_t)aa * im.mu_pitch + bb;
                             const T mu = __ldcg(mu_g + idx);
                             const Dat4<T> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
@@ -445,8 +479,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // the window's first batch is fetched before the prior work so its
             // latency overlaps the arithmetic below
             if (active) {
-                if constexpr (AUG) window_fetch_aug<T>(mu_g, phi_g, im, i, j, muv, phv, lt);
-                else window_fetch<T, CUM>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, lt);
+                if constexpr (AUG) window_fetch_aug<T, FINE>(mu_g, phi_g, im, i, j, muv, phv, lt);
+                else window_fetch<T, CUM, FINE>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, lt);
             }
             // a2 + a4: proposal and prior change (own tile state only)
             if (active) {
@@ -484,9 +518,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // accepted an update since this block last waited for it.
             if (active) {
                 if constexpr (AUG)
-                    lik_partial_aug<T>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane, true);
+                    lik_partial_aug<T, FINE>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane,
+                                             true);
                 else
-                    lik_partial<T, RES, CUM>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
+                    lik_partial<T, RES, CUM, FINE>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
                                              delta, muv, red2 + twarp * 4, lane, cq, cq2, true);
             }
             if (ahead && in_team && twarp == pwarp && q < npt && cs + 1 < ncs) {
@@ -520,10 +555,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             if (r == 0 && s > 0 && s_stale) {
                 if (active) {
                     if constexpr (AUG)
-                        lik_partial_aug<T>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane,
-                                           false);
+                        lik_partial_aug<T, FINE>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4,
+                                                 lane, false);
                     else
-                        lik_partial<T, RES, CUM>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
+                        lik_partial<T, RES, CUM, FINE>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
                                                  delta, muv, red2 + twarp * 4, lane, cq, cq2, false);
                 }
                 __syncthreads();
@@ -548,13 +583,13 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
 #pragma unroll
                         for (int jj = 0; jj < kMaxPx; ++jj) {
                             const int k = k0 + jj * NT;
-                            const int aa = i - 2 * R + k / L, bb = j - 2 * R + (k - (k / L) * L);
-                            if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
+                            int aa, bb, kw;
+                            if (win_cell<FINE>(im, i, j, k, aa, bb, kw)) {
                                 // same value the proposal was scored with: still in registers when
                                 // the window took one batch, else reloaded (unchanged since)
                                 const size_t idx = (size_t)aa * im.mu_pitch + bb;
                                 const T old = one_batch ? muv[jj] : __ldcg(mu_g + idx);
-                                const T xk = mul_rn(delta, Ks[k]);
+                                const T xk = mul_rn(delta, Ks[kw]);
                                 const T nmu = add_rn(old, xk);
                                 __stcg(mu_g + idx, nmu);
                                 if (CUM) {
@@ -650,19 +685,32 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     }
 }
 
-// Raise the kernel's dynamic shared-memory limit to at least smem (the limit
-// only grows, so launches with smaller plans stay valid).
-template <typename T, bool RES, bool AUG>
-cudaError_t ensure_smem_limit(size_t smem)
+// The sweep kernel's form: tile state resident in shared memory or not,
+// augmented sampler or not, object lattice finer than the camera or not.
+template <typename T>
+const void* sweep_fn(bool res, bool aug, bool fine)
 {
-    static std::atomic<size_t> limit{0};
+    if (fine) {
+        if (aug) return res ? (const void*)k_sweep<T, true, true, true> : (const void*)k_sweep<T, false, true, true>;
+        return res ? (const void*)k_sweep<T, true, false, true> : (const void*)k_sweep<T, false, false, true>;
+    }
+    if (aug) return res ? (const void*)k_sweep<T, true, true, false> : (const void*)k_sweep<T, false, true, false>;
+    return res ? (const void*)k_sweep<T, true, false, false> : (const void*)k_sweep<T, false, false, false>;
+}
+
+// Raise a kernel form's dynamic shared-memory limit to at least smem (the
+// limit only grows, so launches with smaller plans stay valid).
+template <typename T>
+cudaError_t ensure_smem_limit(bool res, bool aug, bool fine, size_t smem)
+{
+    static std::atomic<size_t> limit[8];
     static std::mutex mu;
-    if (limit.load() >= smem) return cudaSuccess;
+    const int form = (res ? 1 : 0) | (aug ? 2 : 0) | (fine ? 4 : 0);
+    if (limit[form].load() >= smem) return cudaSuccess;
     std::lock_guard<std::mutex> lock(mu);
-    if (limit.load() >= smem) return cudaSuccess;
-    cudaError_t e =
-        cudaFuncSetAttribute((const void*)k_sweep<T, RES, AUG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) limit.store(smem);
+    if (limit[form].load() >= smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(sweep_fn<T>(res, aug, fine), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) limit[form].store(smem);
     return e;
 }
 
@@ -674,10 +722,8 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
 {
     SweepArgs args = a;
     void* kargs[] = {&args};
-    const void* fn = a.aug ? (a.resident ? (const void*)k_sweep<T, true, true> : (const void*)k_sweep<T, false, true>)
-                           : (a.resident ? (const void*)k_sweep<T, true, false> : (const void*)k_sweep<T, false, false>);
-    cudaError_t e = a.aug ? (a.resident ? ensure_smem_limit<T, true, true>(smem) : ensure_smem_limit<T, false, true>(smem))
-                          : (a.resident ? ensure_smem_limit<T, true, false>(smem) : ensure_smem_limit<T, false, false>(smem));
+    const void* fn = sweep_fn<T>(a.resident, a.aug, a.fine);
+    cudaError_t e = ensure_smem_limit<T>(a.resident, a.aug, a.fine, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -695,23 +741,17 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
 // Blocks of the sweep kernel resident per SM for this block size and shared
 // memory (the smaller of its resident and streamed forms, so either fits).
 template <typename T>
-int sweep_blocks_per_sm(int threads, size_t smem, bool aug)
+int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine)
 {
-    const void* fns[2] = {aug ? (const void*)k_sweep<T, true, true> : (const void*)k_sweep<T, true, false>,
-                          aug ? (const void*)k_sweep<T, false, true> : (const void*)k_sweep<T, false, false>};
-    const cudaError_t e = aug ? (ensure_smem_limit<T, true, true>(smem) == cudaSuccess ? ensure_smem_limit<T, false, true>(smem)
-                                                                                        : cudaErrorInvalidValue)
-                              : (ensure_smem_limit<T, true, false>(smem) == cudaSuccess
-                                     ? ensure_smem_limit<T, false, false>(smem)
-                                     : cudaErrorInvalidValue);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
     int best = 1 << 30;
-    for (const void* fn : fns) {
+    for (int res = 0; res <= 1; ++res) {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, smem) != cudaSuccess) return 0;
+        if (ensure_smem_limit<T>(res != 0, aug, fine, smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_fn<T>(res != 0, aug, fine), threads, smem) != cudaSuccess)
+            return 0;
         best = n < best ? n : best;
     }
     return best;
@@ -719,8 +759,8 @@ int sweep_blocks_per_sm(int threads, size_t smem, bool aug)
 
 template cudaError_t launch_sweep<float>(const SweepArgs&, int, int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs&, int, int, size_t, cudaStream_t);
-template int sweep_blocks_per_sm<float>(int, size_t, bool);
-template int sweep_blocks_per_sm<double>(int, size_t, bool);
+template int sweep_blocks_per_sm<float>(int, size_t, bool, bool);
+template int sweep_blocks_per_sm<double>(int, size_t, bool, bool);
 
 // ---------------------------------------------------------------- delta --
 // The same per-update arithmetic for one hypothetical proposal (testing):
@@ -736,7 +776,7 @@ __global__ void __launch_bounds__(256) k_delta(const Image* imp, const Chain* ch
     const int lt = threadIdx.x, lane = lt & 31, twarp = lt >> 5;
     const int NT = im.team, nwt = NT >> 5;
     const int i = (int)(m / im.Wo), j = (int)(m % im.Wo);
-    const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W, LL = L * L;
+    const int S = im.S, W = im.W, LL = im.Lc * im.Lc;
     const int pi = i / S, pj = j / S, u = i - pi * S, v = j - pj * S;
     const Shape& sh = im.shape[shape_index(im, pi, pj)];
     const T* rho = reinterpret_cast<const T*>(ch.rho);
@@ -758,10 +798,10 @@ __global__ void __launch_bounds__(256) k_delta(const Image* imp, const Chain* ch
     for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx)
         for (int jj = 0; jj < kMaxPx; ++jj) {
             const int k = k0 + jj * NT;
-            const int aa = i - 2 * R + k / L, bb = j - 2 * R + k % L;
-            if (k < LL && (unsigned)aa < (unsigned)H && (unsigned)bb < (unsigned)W) {
+            int aa, bb, kw;
+            if (im.f > 1 ? win_cell<true>(im, i, j, k, aa, bb, kw) : win_cell<false>(im, i, j, k, aa, bb, kw)) {
                 const size_t idx = (size_t)aa * im.mu_pitch + bb;
-                const T xk = mul_rn(delta, K[k]);
+                const T xk = mul_rn(delta, K[kw]);
                 if (std::is_same<T, float>::value && ch.cum) {
                     const float d = (float)xk * Prec<float>::rcp((float)mu[idx]);
                     if (fabsf(d) <= kCumEval) {

@@ -33,6 +33,7 @@ namespace {
 struct ProbHost {
     bdecon_problem p;           // copy (host pointers not retained)
     int H, W, L, R, S, Ho, Wo, npi, npj, n_patches, pitch;
+    int f = 1, Le = 0, Lc = 0;  // lattice cells per camera pixel side, effective kernel side, window side
     int tpi = 1, tpj = 1;       // tile shape in patches
     bool user_plan = false;
     int64_t n_sum = 0;          // sweeps averaged so far
@@ -43,6 +44,7 @@ struct ProbHost {
     int n_tw = 0;               // complex twiddle entries
     int max_nhalf = 0;
     // arena offsets (bytes)
+    size_t o_Ke64 = 0, o_Ke32 = 0;
     size_t o_K64, o_K32, o_dat64, o_dat32, o_ekl, o_wa64, o_m64, o_wa32, o_m32, o_tw64, o_tw32, o_poff;
     size_t o_sum, o_sq, o_scr, o_samp, o_adapt;
     int samp_first = 0;         // first valid kept-object slot (after a resume)
@@ -62,6 +64,7 @@ struct Group {
     int resident = 1;
     bool streamed = false;             // plan with tile state in global memory even if it fits in shared
     bool aug = false;                  // photon-count augmented problems (their own kernel form)
+    bool fine = false;                 // object lattices finer than the camera (their own kernel form)
     int chain_off = 0, n_chains = 0;   // slice of the group-ordered chain table
 };
 
@@ -158,9 +161,12 @@ bdecon_status validate(const bdecon_problem& p, int idx)
     if (!p.image || !p.psf) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: image and psf are required", idx);
     if (p.L < 1 || p.L > kMaxL || p.L % 2 == 0)
         return fail(nullptr, BDECON_ERR_INVALID, "problem %d: PSF side %d must be odd and <= %d", idx, p.L, kMaxL);
-    const int S = p.stride ? p.stride : p.L;
-    if (S < p.L || S > kMaxS)
-        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: stride %d must be in [L=%d, %d]", idx, S, p.L, kMaxS);
+    if (p.subpixel < 0 || p.subpixel > 8) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: subpixel %d", idx, p.subpixel);
+    const int f = p.subpixel > 1 ? p.subpixel : 1, Le = p.L + f - 1;
+    const int S = p.stride ? p.stride : Le;
+    if (S < Le || S > kMaxS)
+        return fail(nullptr, BDECON_ERR_INVALID, "problem %d: stride %d must be in [L + subpixel - 1 = %d, %d]", idx, S,
+                    Le, kMaxS);
     if (p.n_chains < 1 || p.n_chains > 4096) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: n_chains %d", idx, p.n_chains);
     if (p.team_warps < 0 || p.team_warps > 8) return fail(nullptr, BDECON_ERR_INVALID, "problem %d: team_warps %d", idx, p.team_warps);
     if (!(p.adapt_target >= 0.0 && p.adapt_target < 1.0))
@@ -213,8 +219,11 @@ void describe(ProbHost& ph)
 {
     const bdecon_problem& p = ph.p;
     ph.H = p.H; ph.W = p.W; ph.L = p.L; ph.R = p.L / 2;
-    ph.S = p.stride ? p.stride : p.L;
-    ph.Ho = p.H + 2 * ph.R; ph.Wo = p.W + 2 * ph.R;
+    ph.f = p.subpixel > 1 ? p.subpixel : 1;
+    ph.Le = p.L + ph.f - 1;
+    ph.Lc = (ph.Le - 1) / ph.f + 1;
+    ph.S = p.stride ? p.stride : ph.Le;
+    ph.Ho = ph.f * p.H + 2 * ph.R; ph.Wo = ph.f * p.W + 2 * ph.R;
     ph.npi = (ph.Ho + ph.S - 1) / ph.S; ph.npj = (ph.Wo + ph.S - 1) / ph.S;
     ph.n_patches = ph.npi * ph.npj;
     ph.pitch = (int)align_up((size_t)p.W, 4);
@@ -253,10 +262,10 @@ void describe(ProbHost& ph)
     ph.spec_len = off;
 }
 
-int occupancy(int prec, int threads, size_t smem, bool aug)
+int occupancy(int prec, int threads, size_t smem, bool aug, bool fine)
 {
-    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug)
-                               : sweep_blocks_per_sm<double>(threads, smem, aug);
+    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug, fine)
+                               : sweep_blocks_per_sm<double>(threads, smem, aug, fine);
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -281,8 +290,8 @@ size_t items_smem(const std::vector<PlanItem*>& items, int resident, int ts)
     size_t mx = 0;
     for (const PlanItem* it : items) {
         const ProbHost& ph = *it->ph;
-        const SmemPlan sp = smem_plan(ph.L, ph.S, ph.n_tw, (int)ph.ent_kl.size(), ph.max_nhalf, it->tpi, it->tpj,
-                                      resident, ts);
+        const SmemPlan sp = smem_plan(ph.L, ph.f, ph.S, ph.n_tw, (int)ph.ent_kl.size(), ph.max_nhalf, it->tpi,
+                                      it->tpj, resident, ts);
         mx = std::max(mx, sp.total);
     }
     return mx;
@@ -326,7 +335,7 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
             int tot = 0;
             for (const PlanItem* it : items) tot += item_blocks(*it);
             if (smem <= kMaxSmem) {
-                const int bps = occupancy(precision, g.threads, smem, g.aug);
+                const int bps = occupancy(precision, g.threads, smem, g.aug, g.fine);
                 if (bps > 0 && tot <= bps * sms) {
                     g.smem = smem;
                     g.resident = resident;
@@ -417,8 +426,9 @@ void form_groups(bdecon_handle* h)
     for (int k = 0; k < n; ++k) {
         int gi = -1;
         const bool aug = (h->probs[k].p.flags & BDECON_FLAG_AUGMENTED) != 0;
+        const bool fine = h->probs[k].f > 1;
         for (size_t q = 0; q < h->groups.size() && gi < 0; ++q)
-            if (h->groups[q].aug == aug &&
+            if (h->groups[q].aug == aug && h->groups[q].fine == fine &&
                 (h->one_launch || (h->groups[q].L == h->probs[k].L && h->groups[q].S == h->probs[k].S &&
                                    h->groups[q].team == h->imgs[k].team)))
                 gi = (int)q;
@@ -428,6 +438,7 @@ void form_groups(bdecon_handle* h)
             g.S = h->probs[k].S;
             g.team = h->imgs[k].team;
             g.aug = aug;
+            g.fine = fine;
             h->groups.push_back(g);
             gi = (int)h->groups.size() - 1;
         }
@@ -447,6 +458,10 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
         const size_t npix = (size_t)ph.H * ph.W, nobj = (size_t)ph.Ho * ph.Wo, nh = ph.ent_kl.size();
         ph.o_K64 = A.take(8 * ph.L * ph.L);
         ph.o_K32 = A.take(4 * ph.L * ph.L);
+        if (ph.f > 1) {
+            ph.o_Ke64 = A.take(8 * (size_t)ph.Le * ph.Le);
+            ph.o_Ke32 = A.take(4 * (size_t)ph.Le * ph.Le);
+        }
         ph.o_dat64 = A.take(32 * npix);
         ph.o_dat32 = A.take(16 * npix);
         ph.o_ekl = A.take(4 * nh);
@@ -599,6 +614,9 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         im.n_patches = ph.n_patches; im.chain0 = ph.chain0;
         char* A = h->arena;
         im.K64 = (const double*)(A + ph.o_K64); im.K32 = (const float*)(A + ph.o_K32);
+        im.f = ph.f; im.Le = ph.Le; im.Lc = ph.Lc;
+        im.Ke64 = ph.f > 1 ? (const double*)(A + ph.o_Ke64) : im.K64;
+        im.Ke32 = ph.f > 1 ? (const float*)(A + ph.o_Ke32) : im.K32;
         im.dat64 = (const double*)(A + ph.o_dat64); im.dat32 = (const float*)(A + ph.o_dat32);
         for (int s = 0; s < kMaxShapes; ++s) im.shape[s] = ph.shape[s];
         im.ent_kl = (const int*)(A + ph.o_ekl);
@@ -608,7 +626,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         im.patch_off = (const int64_t*)(A + ph.o_poff);
         im.spec_len = ph.spec_len;
         im.n_ent = (int)ph.ent_kl.size();
-        im.team = problem_team(ph.L, ph.p.n_chains, ph.n_patches, ph.p.team_warps);
+        im.team = problem_team(ph.Lc, ph.p.n_chains, ph.n_patches, ph.p.team_warps);
         im.n_tw = ph.n_tw;
         im.max_nhalf = ph.max_nhalf;
         im.sample_every = ph.p.sample_every > 0 ? ph.p.sample_every : 1;
@@ -821,6 +839,7 @@ bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle
         a.n_sweeps = len; a.err = eh->d_err; a.resident = g.resident;
         a.wait_ns = eh->wait_ns; a.silent_block = gi == 0 ? eh->silent_block : -1;
         a.aug = g.aug ? 1 : 0;
+        a.fine = g.fine ? 1 : 0;
         cudaError_t e = eh->precision == BDECON_FP32 ? launch_sweep<float>(a, g.grid, g.threads, g.smem, st)
                                                      : launch_sweep<double>(a, g.grid, g.threads, g.smem, st);
         if (e != cudaSuccess)
@@ -1041,7 +1060,7 @@ bdecon_status bdecon_posterior_mean(bdecon_handle* h, int32_t p, double* out, in
     if (s != BDECON_OK) return s;
     ProbHost& ph = h->probs[p];
     if (ph.n_sum == 0) return fail(h, BDECON_ERR_STATE, "no sweep after burn-in yet");
-    const int oh = crop ? ph.H : ph.Ho, ow = crop ? ph.W : ph.Wo;
+    const int oh = crop ? ph.f * ph.H : ph.Ho, ow = crop ? ph.f * ph.W : ph.Wo;
     launch_mean(h->chains[ci].rho_sum, ph.p.n_chains, (int64_t)ph.Ho * ph.Wo, ph.Ho, ph.Wo, crop ? ph.R : 0, oh, ow,
                 1.0 / ((double)ph.n_sum * ph.p.n_chains), h->d_up, nullptr, 0, h->st, &h->launches);
     CK(h, cudaMemcpyAsync(out, h->d_up, 8 * (size_t)oh * ow, cudaMemcpyDeviceToHost, h->st));
@@ -1060,7 +1079,7 @@ bdecon_status pooled_map(bdecon_handle* h, int32_t p, double* out, int32_t crop,
     ProbHost& ph = h->probs[p];
     if (kind > 0 && !ph.o_sq) return fail(h, BDECON_ERR_STATE, "created without BDECON_FLAG_SECOND_MOMENT");
     if (ph.n_sum == 0) return fail(h, BDECON_ERR_STATE, "no sweep after burn-in yet");
-    const int oh = crop ? ph.H : ph.Ho, ow = crop ? ph.W : ph.Wo;
+    const int oh = crop ? ph.f * ph.H : ph.Ho, ow = crop ? ph.f * ph.W : ph.Wo;
     launch_mean(h->chains[ci].rho_sum, ph.p.n_chains, (int64_t)ph.Ho * ph.Wo, ph.Ho, ph.Wo, crop ? ph.R : 0, oh, ow,
                 1.0 / ((double)ph.n_sum * ph.p.n_chains), h->d_up, h->chains[ci].rho_sq, kind, h->st, &h->launches);
     CK(h, cudaMemcpyAsync(out, h->d_up, 8 * (size_t)oh * ow, cudaMemcpyDeviceToHost, h->st));
@@ -1136,7 +1155,7 @@ bdecon_status bdecon_posterior_quantiles(bdecon_handle* h, int32_t p, const doub
         return fail(h, BDECON_ERR_INVALID, "%d kept values per pixel, at most %d", count * ph.p.n_chains, kMaxQuantileValues);
     s = check_device(h);
     if (s != BDECON_OK) return s;
-    const int oh = crop ? ph.H : ph.Ho, ow = crop ? ph.W : ph.Wo;
+    const int oh = crop ? ph.f * ph.H : ph.Ho, ow = crop ? ph.f * ph.W : ph.Wo;
     const int64_t npix = (int64_t)oh * ow, nobj = (int64_t)ph.Ho * ph.Wo;
     // staging in d_up: the probabilities, then nq values per pixel of a chunk
     double* dq = h->d_up;
@@ -1684,12 +1703,13 @@ bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
         const ProbHost& ph = h->probs[ent[e].pk];
         const int team = h->imgs[ent[e].pk].team;
         const int aug = ph.p.flags & BDECON_FLAG_AUGMENTED;
+        const bool fine = ph.f > 1;
         int gi = -1;
         for (size_t q = 0; q < groups.size() && gi < 0; ++q) {
             const Entry& f = ent[groups[q][0]];
             const bdecon_handle* h2 = ls.hs[f.hi];
             const ProbHost& ph2 = h2->probs[f.pk];
-            if ((ph2.p.flags & BDECON_FLAG_AUGMENTED) == aug &&
+            if ((ph2.p.flags & BDECON_FLAG_AUGMENTED) == aug && (ph2.f > 1) == fine &&
                 (S->cfg.one_launch || (ph2.L == ph.L && ph2.S == ph.S && h2->imgs[f.pk].team == team)))
                 gi = (int)q;
         }
@@ -1716,6 +1736,7 @@ bool srv_build(bdecon_server* S, LaunchSet& ls, std::vector<Image>& imgs)
     for (auto& gidx : groups) {
         Group g;
         g.aug = (ls.hs[ent[gidx[0]].hi]->probs[ent[gidx[0]].pk].p.flags & BDECON_FLAG_AUGMENTED) != 0;
+        g.fine = ls.hs[ent[gidx[0]].hi]->probs[ent[gidx[0]].pk].f > 1;
         std::vector<PlanItem> items(gidx.size());
         std::vector<PlanItem*> ptrs;
         for (size_t q = 0; q < gidx.size(); ++q) {

@@ -34,7 +34,7 @@ def _problem_struct(prob, **over):
     psf = np.ascontiguousarray(prob.psf, dtype=np.float64)
     keep = [img, psf]
     p = bdecon._Problem(prob.H, prob.W, img.ctypes.data, prob.L, psf.ctypes.data, None, 2.0, None, 100.0,
-                        None, 2.56, 0, 1, 0, 0.2, 0, 10, bdecon.BDECON_FP32, 64, 0, 0, 0, 0, 0.0)
+                        None, 2.56, 0, 1, 0, 0.2, 0, 10, bdecon.BDECON_FP32, 64, 0, 0, 0, 0, 0.0, 0)
     for k, v in over.items():
         setattr(p, k, v)
     return p, keep
@@ -55,6 +55,7 @@ def _problem_struct(prob, **over):
     ("n_samples", -1, "n_samples"),
     ("adapt_target", 1.0, "adapt_target"),
     ("adapt_target", float("nan"), "adapt_target"),
+    ("subpixel", 9, "subpixel"),
 ])
 def test_invalid_problem_refused(field, value, msg):
     L = bdecon.load()
