@@ -540,6 +540,29 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     }
                 }
             }
+            // a5: Metropolis-Hastings decision with the Hastings term of the log-space
+            // walk, taken from the round's partial sums as soon as every warp has
+            // written them -- before the neighbour wait, so that a rejected update
+            // (the common case) leaves only the wait and the publish after it
+            __syncthreads();
+            T dL = 0, dP = 0;
+            bool accept = false;
+            auto decide = [&]() {
+                T sP = 0, sS = 0, sA = 0;
+                bool bad = false;
+                dL = 0;
+                for (int w = 0; w < nwt; ++w) {
+                    sP += red1[w * 4 + 0];
+                    sS += red1[w * 4 + 1];
+                    sA += red1[w * 4 + 2];
+                    bad = bad || red1[w * 4 + 3] != (T)0;
+                    dL += red2[w * 4 + 0];
+                    bad = bad || red2[w * 4 + 1] != (T)0;
+                }
+                dP = sP + (T)(sh.K - 1) * P::log1p(sS / sA);
+                accept = !bad && (lu < dL + dP + z);   // z holds s_m z
+            };
+            if (active) decide();
             if (r == 0 && s > 0 && tid < 32) {
                 bool stale = false;
                 const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns);
@@ -550,9 +573,12 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     s_stale = stale ? 1 : 0;
                 }
             }
-            __syncthreads();
+            // (the partial sums are not read after this barrier, so the next round
+            // may overwrite them; writes of an accepted update need one more)
+            const int any_accept = __syncthreads_or(active && accept ? 1 : 0);
             if (s_abort) return;
-            if (r == 0 && s > 0 && s_stale) {
+            const bool stale = r == 0 && s > 0 && s_stale;
+            if (stale) {
                 if (active) {
                     if constexpr (AUG)
                         lik_partial_aug<T, FINE>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4,
@@ -562,21 +588,9 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                                                  delta, muv, red2 + twarp * 4, lane, cq, cq2, false);
                 }
                 __syncthreads();
+                if (active) decide();
             }
-            // a5: Metropolis-Hastings decision with the Hastings term of the log-space walk
             if (active) {
-                T sP = 0, sS = 0, sA = 0, dL = 0;
-                bool bad = false;
-                for (int w = 0; w < nwt; ++w) {
-                    sP += red1[w * 4 + 0];
-                    sS += red1[w * 4 + 1];
-                    sA += red1[w * 4 + 2];
-                    bad = bad || red1[w * 4 + 3] != (T)0;
-                    dL += red2[w * 4 + 0];
-                    bad = bad || red2[w * 4 + 1] != (T)0;
-                }
-                const T dP = sP + (T)(sh.K - 1) * P::log1p(sS / sA);
-                const bool accept = !bad && (lu < dL + dP + z);   // z holds s_m z
                 if (accept) {
                     const bool one_batch = LL <= NT * kMaxPx;
                     for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
@@ -630,7 +644,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     sg[m] = sn < (T)1e-4 ? (T)1e-4 : sn > (T)4 ? (T)4 : sn;
                 }
             }
-            __syncthreads();
+            if (stale || any_accept) __syncthreads();
         }
         if (c == S2 - 1) {
             // a7: after the sweep, add the object to the running sums (own
