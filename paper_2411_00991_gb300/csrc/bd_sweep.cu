@@ -164,8 +164,12 @@ __device__ __forceinline__ void lik_partial(const T* mu_g, const float4* cum_g, 
 #pragma unroll
         for (int jj = 0; jj < kMaxPx; ++jj) {
             const int k = k0 + jj * NT;
-            int aa, bb, kw;
-            if (win_cell<FINE>(im, i, j, k, aa, bb, kw)) {
+            // on the camera grid the fetched window tells the cells apart (mu > 0
+            // inside, -1 outside), so the geometry is needed only to read the
+            // cell's data on the exact path; the finer lattice needs its PSF index
+            int aa = 0, bb = 0, kw = k;
+            const bool in = FINE ? win_cell<FINE>(im, i, j, k, aa, bb, kw) : muv[jj] != (T)-1;
+            if (in) {
                 const T xk = mul_rn(delta, Ks[kw]);
                 if (CUM) {
                     const float d = (float)xk * Prec<float>::rcp((float)muv[jj]);
@@ -174,6 +178,7 @@ __device__ __forceinline__ void lik_partial(const T* mu_g, const float4* cum_g, 
                         continue;
                     }
                 }
+                if (!FINE) win_cell<FINE>(im, i, j, k, aa, bb, kw);
                 const Dat4<T> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
                 if (CUM) {
                     int b = 0;
@@ -228,8 +233,9 @@ __device__ __forceinline__ void lik_partial_aug(const T* mu_g, const T* phi_g, c
 #pragma unroll
         for (int jj = 0; jj < kMaxPx; ++jj) {
             const int k = k0 + jj * NT;
-            int aa, bb, kw;
-            if (win_cell<FINE>(im, i, j, k, aa, bb, kw)) {
+            int aa = 0, bb = 0, kw = k;
+            const bool in = FINE ? win_cell<FINE>(im, i, j, k, aa, bb, kw) : muv[jj] != (T)-1;
+            if (in) {
                 const T xk = mul_rn(delta, Ks[kw]);
                 const T d = xk / muv[jj];
                 if (!(d > (T)-1)) {
