@@ -188,6 +188,60 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
     return __all_sync(0xffffffffu, ok);
 }
 
+// ------------------------------------------- bulk copies (TMA engine) --
+// Global -> shared copies issued to the tensor memory accelerator as
+// untiled bulk copies (cp.async.bulk), completing on a shared-memory
+// mbarrier that counts the bytes still to land.  Both addresses must be
+// 16-byte aligned and the size a multiple of 16 bytes; the callers copy
+// rows of 16- or 32-byte records between 16-byte-aligned bases.
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the async proxy that completes it
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Bounded wait for phase `parity` of the barrier to complete: false after
+// wait_ns nanoseconds or 2^26 tries.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t wait_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 1; it <= kWaitPolls; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0u && global_ns() - t0 > wait_ns) break;
+    }
+    return false;
+}
+
 // ------------------------------------------- photon-count augmentation --
 // Draw of a photon count from p(phi | w, mu) ∝ exp(-(c - phi)^2 is2 / 2)
 // mu^phi / phi!  (the summands of Eq. 6: Normal(w; G phi + o, var) times

@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     __shared__ int s_acc_any;
     __shared__ T s_prop[2][8][4];   // next-step proposals of one-patch teams: z, log u, rho', delta
     __shared__ double s_phid[AUG ? 8 : 1][8];   // photon-count step: [sub-team][warp] log-density changes
+    __shared__ __align__(8) uint64_t s_bar;      // completion of the tile's bulk copies (resident plans)
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -334,6 +335,24 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         s_abort = 0;
         s_stale = 0;
         s_acc_any = 0;
+        if (RES) mbar_init(&s_bar, 1);
+    }
+    // Resident plans: the tile's per-pixel constants -- camera rows a_lo..a_hi-1,
+    // columns b_lo..b_hi-1, i.e. the tile's windows with the PSF halo -- are
+    // staged in shared memory by bulk copies of the TMA engine, one per row (rw
+    // records of 16 or 32 bytes, 16-byte-aligned at both ends), issued by the
+    // first warp and overlapped with the table loads below
+    const int n_rows = RES ? a_hi - a_lo : 0;
+    const bool staged = RES && n_rows > 0 && rw > 0;
+    if (RES) {
+        __syncthreads();   // barrier initialised
+        if (staged && tid < 32) {
+            const uint32_t row_bytes = (uint32_t)rw * (uint32_t)sizeof(Dat4<T>);
+            if (tid == 0) mbar_arrive_expect_tx(&s_bar, (uint32_t)n_rows * row_bytes);
+            __syncwarp();
+            for (int r = tid; r < n_rows; r += 32)
+                bulk_g2s(dat_s + (size_t)r * rw, dat_g + (size_t)(a_lo + r) * W + b_lo, row_bytes, &s_bar);
+        }
     }
     for (int k = tid; k < Le * Le; k += blockDim.x) Ks[k] = kern<T>(im)[k];
     for (int k = tid; k < 2 * im.n_tw; k += blockDim.x) tws[k] = twid<T>(im)[k];
@@ -343,10 +362,6 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         em[k] = ent_m<T>(im)[k];
     }
     if (RES) {
-        for (int k = tid; k < (a_hi - a_lo) * rw; k += blockDim.x) {
-            const int aa = k / rw, bb = k - (k / rw) * rw;
-            dat_s[k] = dat_g[(size_t)(a_lo + aa) * W + b_lo + bb];
-        }
         for (int q = 0; q < npt; ++q) {
             const int pi = pi0 + q / tw_, pj = pj0 + (q - (q / tw_) * tw_);
             const Shape& sh = im.shape[shape_index(im, pi, pj)];
@@ -358,7 +373,17 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             }
         }
     }
+    if (staged && !mbar_wait(&s_bar, 0, a.wait_ns)) {
+        atomicOr(a.err, kErrTimeout);
+        s_abort = 1;
+    }
     __syncthreads();
+    if (s_abort) {
+        // the copies were not seen to land: give them one more bounded wait
+        // before the block's shared memory is released
+        if (staged) (void)mbar_wait(&s_bar, 0, a.wait_ns);
+        return;
+    }
 
     const int NT = im.team;
     const int n_sub = max(1, (int)blockDim.x / NT);
