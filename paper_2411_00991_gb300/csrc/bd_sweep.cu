@@ -400,8 +400,9 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     const int nsteps = nsw * SS, ncs = nsw * S2;
     int n_acc = 0;
     // with one update per team and step, a warp of the team draws the next
-    // step's proposal ahead of time (before the neighbour wait); not when a
-    // patch has a single class (S = 1), where the next step revisits the pixel
+    // step's proposal ahead of time, while the polling warp waits for the
+    // neighbours; not when a patch has a single class (S = 1), where the next
+    // step revisits the pixel
     const bool ahead = rounds == 1 && S2 > 1;
     const int pwarp = nwt > 1 ? 1 : 0;   // the drawing warp: not the one that polls the flags
     if (ahead && in_team && twarp == pwarp && g < npt && ncs > 0) {
@@ -555,22 +556,6 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     lik_partial<T, RES, CUM, FINE>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
                                              delta, muv, red2 + twarp * 4, lane, cq, cq2, true);
             }
-            if (ahead && in_team && twarp == pwarp && q < npt && cs + 1 < ncs) {
-                const int s1 = cs + 1, c1 = s1 % S2;
-                const int u1 = c1 / S, v1 = c1 - (c1 / S) * S;
-                const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
-                const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
-                if (u1 < sh1.ph && v1 < sh1.pw) {
-                    const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
-                    T z1, lu1, rn1, dl1;
-                    proposal<T>(im, ch, m1, t0 + 1 + s1 / S2, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1],
-                                z1, lu1, rn1, dl1);
-                    if (lane == 0) {
-                        s_prop[s1 & 1][g][0] = z1; s_prop[s1 & 1][g][1] = lu1;
-                        s_prop[s1 & 1][g][2] = rn1; s_prop[s1 & 1][g][3] = dl1;
-                    }
-                }
-            }
             // a5: Metropolis-Hastings decision with the Hastings term of the log-space
             // walk, taken from the round's partial sums as soon as every warp has
             // written them -- before the neighbour wait, so that a rejected update
@@ -594,6 +579,24 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 accept = !bad && (lu < dL + dP + z);   // z holds s_m z
             };
             if (active) decide();
+            // the next step's draw, after the step barrier so that the other warps
+            // need not wait for it there; it overlaps the neighbour wait below
+            if (ahead && in_team && twarp == pwarp && q < npt && cs + 1 < ncs) {
+                const int s1 = cs + 1, c1 = s1 % S2;
+                const int u1 = c1 / S, v1 = c1 - (c1 / S) * S;
+                const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
+                const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
+                if (u1 < sh1.ph && v1 < sh1.pw) {
+                    const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
+                    T z1, lu1, rn1, dl1;
+                    proposal<T>(im, ch, m1, t0 + 1 + s1 / S2, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1],
+                                z1, lu1, rn1, dl1);
+                    if (lane == 0) {
+                        s_prop[s1 & 1][g][0] = z1; s_prop[s1 & 1][g][1] = lu1;
+                        s_prop[s1 & 1][g][2] = rn1; s_prop[s1 & 1][g][3] = dl1;
+                    }
+                }
+            }
             if (r == 0 && s > 0 && tid < 32) {
                 bool stale = false;
                 const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns);
