@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     __shared__ int s_ci;
     __shared__ int s_stale;
     __shared__ int s_acc_any;
+    __shared__ int s_pub;
     __shared__ T s_prop[2][8][4];   // next-step proposals of one-patch teams: z, log u, rho', delta
     __shared__ double s_phid[AUG ? 8 : 1][8];   // photon-count step: [sub-team][warp] log-density changes
     __shared__ __align__(8) uint64_t s_bar;      // completion of the tile's bulk copies (resident plans)
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         s_abort = 0;
         s_stale = 0;
         s_acc_any = 0;
+        s_pub = 0;
         if (RES) mbar_init(&s_bar, 1);
     }
     // Resident plans: the tile's per-pixel constants -- camera rows a_lo..a_hi-1,
@@ -405,6 +407,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     // step revisits the pixel
     const bool ahead = rounds == 1 && S2 > 1;
     const int pwarp = nwt > 1 ? 1 : 0;   // the drawing warp: not the one that polls the flags
+    // one update per block and step (rounds == 1, n_sub == 1): a rejected
+    // update scored on the neighbours' final state leaves nothing to write or
+    // reread, so thread 0 publishes the step as soon as its wait ends
+    // (s_pub: already published; thread 0 only)
     if (ahead && in_team && twarp == pwarp && g < npt && ncs > 0) {
         const int pi = pi0 + g / tw_, pj = pj0 + (g - (g / tw_) * tw_);
         const Shape& sh = im.shape[shape_index(im, pi, pj)];
@@ -605,6 +611,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 if (lane == 0) {
                     if (!ok) s_abort = 1;
                     s_stale = stale ? 1 : 0;
+                    if (ok && !stale && !accept && rounds == 1 && n_sub == 1 && (int)blockIdx.x != a.silent_block) {
+                        st_relaxed(ch.prog + tl, s + 1);
+                        s_pub = 1;
+                    }
                 }
             }
             // (the partial sums are not read after this barrier, so the next round
@@ -713,7 +723,9 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // (a step without an accepted update wrote nothing the neighbours
             // read, and its own reads were consumed before the barrier, so a
             // plain store suffices; otherwise release the mu writes)
-            if (s_acc_any) {
+            if (s_pub) {
+                s_pub = 0;
+            } else if (s_acc_any) {
                 ch.acc_step[tl] = s + 1;
                 s_acc_any = 0;
                 st_release(ch.prog + tl, s + 1);
