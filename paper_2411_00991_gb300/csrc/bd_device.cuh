@@ -151,26 +151,37 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Bounded wait of one warp until prog[nbr[i]] >= need for every i < nn.
-// Gives up (setting kErrTimeout) after wait_ns nanoseconds (default 4 s) or
-// 2^26 polls, or as soon as any other block has raised an error.  Returns
-// true if every flag arrived.
+// Progress word of a tile: (steps published << 2) | c0 | c1 << 1, c0 (c1)
+// set when the tile changed data its neighbours' windows read (an accepted
+// update, or the photon counts) at the last (the one before the last)
+// published step.  One word carries both the step count a neighbour waits
+// for and what it needs to know whether its speculative score went stale.
+__device__ __forceinline__ int prog_word(int steps, bool changed, bool changed_before)
+{
+    return (steps << 2) | (changed ? 1 : 0) | (changed_before ? 2 : 0);
+}
+
+// Bounded wait of one warp until every neighbour nbr[i] (i < nn, one per
+// lane) has published at least `need` steps.  Gives up (setting kErrTimeout)
+// after wait_ns nanoseconds (default 4 s) or 2^26 polls, or as soon as any
+// other block has raised an error.  Returns true if every flag arrived; word
+// receives the lane's neighbour word (acquire load, after the wait).
 constexpr uint64_t kWaitNs = 4000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 26;
-
 __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr, int nn, int need,
-                                                int* err, uint64_t wait_ns = kWaitNs)
+                                                int* err, uint64_t wait_ns, int& word)
 {
     const int lane = threadIdx.x & 31;
     bool ok = true;
+    word = 0;
     if (lane < nn) {
         const int* f = prog + nbr[lane];
         // poll with relaxed loads (tight for the first polls, then with a short
         // sleep); the final acquire orders the reads of the neighbour's data
-        if (ld_relaxed(f) < need) {
+        if ((ld_relaxed(f) >> 2) < need) {
             const uint64_t t0 = global_ns();
             uint32_t it = 0;
-            while (ld_relaxed(f) < need) {
+            while ((ld_relaxed(f) >> 2) < need) {
                 ++it;
                 if ((it & 31u) == 0u) {
                     if (ld_relaxed(err) != 0) { ok = false; break; }
@@ -183,7 +194,7 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
                 if (it > 64u) __nanosleep(32);
             }
         }
-        if (ok) (void)ld_acquire(f);
+        if (ok) word = ld_acquire(f);
     }
     return __all_sync(0xffffffffu, ok);
 }

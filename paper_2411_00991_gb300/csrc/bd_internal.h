@@ -74,8 +74,7 @@ struct Chain {
     double* trace_part;              // [slot][patch] accepted dL + dP
     unsigned long long* acc_count;   // [sweep - 1]
     uint8_t* acc_log;                // [sweep - 1][Ho*Wo] or null
-    int* prog;                       // per tile: steps completed in this launch
-    int* acc_step;                   // per tile: last step (1-based) with an accepted update
+    int* prog;                       // per tile: progress word (steps published in this launch, change marks)
     double* trace;                   // [sweep 0..max_sweeps]
     int tpi, tpj, nti, ntj;          // tile shape (patches) and tile grid
     int cta_base;                    // first block of this chain in the sweep grid

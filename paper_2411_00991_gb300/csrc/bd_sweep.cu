@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     __shared__ int s_stale;
     __shared__ int s_acc_any;
     __shared__ int s_pub;
+    __shared__ int s_chg;   // the last published step changed data (thread 0 only)
     __shared__ T s_prop[2][8][4];   // next-step proposals of one-patch teams: z, log u, rho', delta
     __shared__ double s_phid[AUG ? 8 : 1][8];   // photon-count step: [sub-team][warp] log-density changes
     __shared__ __align__(8) uint64_t s_bar;      // completion of the tile's bulk copies (resident plans)
@@ -337,6 +338,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         s_stale = 0;
         s_acc_any = 0;
         s_pub = 0;
+        s_chg = 0;
         if (RES) mbar_init(&s_bar, 1);
     }
     // Resident plans: the tile's per-pixel constants -- camera rows a_lo..a_hi-1,
@@ -435,7 +437,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 // tile's patches from p(phi | w, mu) (Philox counter (n, t, chain, 1));
                 // the change of the log joint density goes to the patch's trace part
                 if (s > 0 && tid < 32) {
-                    const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns);
+                    int word;
+                    const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns, word);
                     if (lane == 0 && !ok) s_abort = 1;
                 }
                 __syncthreads();
@@ -484,9 +487,9 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 }
                 if (tid == 0 && (int)blockIdx.x != a.silent_block) {
                     // the neighbours' next windows read these counts: mark the step
-                    // (their speculative scores are redone) and release
-                    ch.acc_step[tl] = s + 1;
-                    st_release(ch.prog + tl, s + 1);
+                    // changed (their speculative scores are redone) and release
+                    st_release(ch.prog + tl, prog_word(s + 1, true, s_chg != 0));
+                    s_chg = 1;
                 }
                 continue;
             }
@@ -604,15 +607,20 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 }
             }
             if (r == 0 && s > 0 && tid < 32) {
+                // stale: a neighbour changed data this window reads at its step s-1
+                // (or at step s, whose windows are disjoint from this one: a
+                // harmless recompute), read from the word the wait ended on
+                int word;
+                const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns, word);
                 bool stale = false;
-                const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns);
-                if (ok && lane < s_nn) stale = ld_relaxed(ch.acc_step + s_nbr[lane]) >= s;
+                if (ok && lane < s_nn) stale = (word & ((word >> 2) > s ? 3 : 1)) != 0;
                 stale = __any_sync(0xffffffffu, stale);
                 if (lane == 0) {
                     if (!ok) s_abort = 1;
                     s_stale = stale ? 1 : 0;
                     if (ok && !stale && !accept && rounds == 1 && n_sub == 1 && (int)blockIdx.x != a.silent_block) {
-                        st_relaxed(ch.prog + tl, s + 1);
+                        st_relaxed(ch.prog + tl, prog_word(s + 1, false, s_chg != 0));
+                        s_chg = 0;
                         s_pub = 1;
                     }
                 }
@@ -718,19 +726,20 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             __syncthreads();
         }
         if (tid == 0 && (int)blockIdx.x != a.silent_block) {
-            // publish: the last step with an accepted update (read by the
-            // neighbours' staleness check), then the step count (release)
-            // (a step without an accepted update wrote nothing the neighbours
-            // read, and its own reads were consumed before the barrier, so a
-            // plain store suffices; otherwise release the mu writes)
+            // publish the step count with this step's and the previous step's
+            // change marks (read by the neighbours' staleness check); a step
+            // without an accepted update wrote nothing the neighbours read, and
+            // its own reads were consumed before the barrier, so a plain store
+            // suffices; otherwise release the mu writes
             if (s_pub) {
                 s_pub = 0;
             } else if (s_acc_any) {
-                ch.acc_step[tl] = s + 1;
                 s_acc_any = 0;
-                st_release(ch.prog + tl, s + 1);
+                st_release(ch.prog + tl, prog_word(s + 1, true, s_chg != 0));
+                s_chg = 1;
             } else {
-                st_relaxed(ch.prog + tl, s + 1);
+                st_relaxed(ch.prog + tl, prog_word(s + 1, false, s_chg != 0));
+                s_chg = 0;
             }
         }
     }

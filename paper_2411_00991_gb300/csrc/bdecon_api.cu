@@ -69,7 +69,7 @@ struct Group {
 };
 
 struct ChainHost {
-    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_astep, o_trace, o_tdev, o_steps, o_phi;
+    size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_trace, o_tdev, o_steps, o_phi;
 };
 
 }  // namespace
@@ -496,7 +496,6 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
             x.o_acc = A.take(8 * (size_t)max_sweeps);
             x.o_log = (ph.p.flags & BDECON_FLAG_ACCEPT_LOG) ? A.take((size_t)max_sweeps * nobj) : 0;
             x.o_prog = A.take(4 * (size_t)ph.n_patches);
-            x.o_astep = A.take(4 * (size_t)ph.n_patches);
             x.o_trace = A.take(8 * ((size_t)max_sweeps + 1));
             x.o_tdev = A.take(4);
             x.o_steps = adapt ? A.take(ts * nobj) : 0;
@@ -652,7 +651,6 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
             ch.acc_count = (unsigned long long*)(A + x.o_acc);
             ch.acc_log = x.o_log ? (uint8_t*)(A + x.o_log) : nullptr;
             ch.prog = (int*)(A + x.o_prog);
-            ch.acc_step = (int*)(A + x.o_astep);
             ch.trace = (double*)(A + x.o_trace);
             ch.tdev = (int*)(A + x.o_tdev);
             ch.samples = ph.o_samp ? A + ph.o_samp + (h->precision == BDECON_FP32 ? 4 : 8) * nobj * ph.p.n_samples * c
