@@ -144,6 +144,10 @@ __device__ __forceinline__ int ld_relaxed(const int* p)
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
 __device__ __forceinline__ uint64_t global_ns()
 {
     uint64_t t;
@@ -177,11 +181,13 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
     if (lane < nn) {
         const int* f = prog + nbr[lane];
         // poll with relaxed loads (tight for the first polls, then with a short
-        // sleep); the final acquire orders the reads of the neighbour's data
-        if ((ld_relaxed(f) >> 2) < need) {
+        // sleep); the relaxed load that saw the step, followed by an acquire
+        // fence, orders the reads of the neighbour's data after its release
+        int v = ld_relaxed(f);
+        if ((v >> 2) < need) {
             const uint64_t t0 = global_ns();
             uint32_t it = 0;
-            while ((ld_relaxed(f) >> 2) < need) {
+            while (((v = ld_relaxed(f)) >> 2) < need) {
                 ++it;
                 if ((it & 31u) == 0u) {
                     if (ld_relaxed(err) != 0) { ok = false; break; }
@@ -194,7 +200,10 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
                 if (it > 64u) __nanosleep(32);
             }
         }
-        if (ok) word = ld_acquire(f);
+        if (ok) {
+            fence_acq_rel_gpu();
+            word = v;
+        }
     }
     return __all_sync(0xffffffffu, ok);
 }
