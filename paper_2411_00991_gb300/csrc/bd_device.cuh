@@ -124,12 +124,6 @@ __device__ __forceinline__ T warp_sum(T v)
 }
 
 // ------------------------------------------------------ memory ordering --
-__device__ __forceinline__ int ld_acquire(const int* p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void st_release(int* p, int v)
 {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -169,7 +163,7 @@ __device__ __forceinline__ int prog_word(int steps, bool changed, bool changed_b
 // lane) has published at least `need` steps.  Gives up (setting kErrTimeout)
 // after wait_ns nanoseconds (default 4 s) or 2^26 polls, or as soon as any
 // other block has raised an error.  Returns true if every flag arrived; word
-// receives the lane's neighbour word (acquire load, after the wait).
+// receives the lane's neighbour word as the wait saw it.
 constexpr uint64_t kWaitNs = 4000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 26;
 __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr, int nn, int need,
