@@ -273,7 +273,6 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     __shared__ int s_acc_any;
     __shared__ int s_pub;
     __shared__ int s_chg;   // the last published step changed data (thread 0 only)
-    __shared__ T s_prop[2][8][4];   // next-step proposals of one-patch teams: z, log u, rho', delta
     __shared__ double s_phid[AUG ? 8 : 1][8];   // photon-count step: [sub-team][warp] log-density changes
     __shared__ __align__(8) uint64_t s_bar;      // completion of the tile's bulk copies (resident plans)
 
@@ -313,6 +312,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     int* ekl = reinterpret_cast<int*>(smem + sp.ekl);
     T* ewa = reinterpret_cast<T*>(smem + sp.ewa);
     T* em = reinterpret_cast<T*>(smem + sp.em);
+    T* ring = reinterpret_cast<T*>(smem + sp.prop);         // [team][kPropRing][4] (one-patch teams)
     T* spec_s = reinterpret_cast<T*>(smem + sp.spec);       // [npt][max_nhalf] complex
     T* rho_s = reinterpret_cast<T*>(smem + sp.rho);         // [npt][S*S]
     Dat4<T>* dat_s = reinterpret_cast<Dat4<T>*>(smem + sp.dat);
@@ -407,24 +407,36 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     // step's proposal ahead of time, while the polling warp waits for the
     // neighbours; not when a patch has a single class (S = 1), where the next
     // step revisits the pixel
-    const bool ahead = rounds == 1 && S2 > 1;
+    const bool ahead = rounds == 1 && S2 > 1 && ch.tpi * ch.tpj <= 8;   // (the ring exists for such tiles)
     const int pwarp = nwt > 1 ? 1 : 0;   // the drawing warp: not the one that polls the flags
     // one update per block and step (rounds == 1, n_sub == 1): a rejected
     // update scored on the neighbours' final state leaves nothing to write or
     // reread, so thread 0 publishes the step as soon as its wait ends
     // (s_pub: already published; thread 0 only)
-    if (ahead && in_team && twarp == pwarp && g < npt && ncs > 0) {
-        const int pi = pi0 + g / tw_, pj = pj0 + (g - (g / tw_) * tw_);
-        const Shape& sh = im.shape[shape_index(im, pi, pj)];
-        if (sh.ph > 0 && sh.pw > 0) {
-            const int m = (pi * S) * im.Wo + pj * S;
-            T z, lu, rn, dl;
-            proposal<T>(im, ch, m, t0 + 1, RES ? rho_s[(size_t)g * S2] : rho_g[m], z, lu, rn, dl);
-            if (lane == 0) {
-                s_prop[0][g][0] = z; s_prop[0][g][1] = lu; s_prop[0][g][2] = rn; s_prop[0][g][3] = dl;
+    // one-patch teams draw their proposals ahead: the drawing warp's lanes
+    // fill the ring kPropRing class steps at a time when a sweep has more than
+    // kPropRing classes (a pixel's rho and scale change only at its own update,
+    // once per sweep, so a draw made less than a sweep ahead gives the same
+    // move), else one step ahead (the whole warp on one draw)
+    const bool wide = ahead && S2 > kPropRing;
+    auto draw_ahead = [&](int q, int e0) {
+        const int e = e0 + (wide ? lane : 0);            // class-step ordinal of the draw
+        const int sw = e / S2, cl = e - sw * S2;
+        const int u1 = cl / S, v1 = cl - (cl / S) * S;
+        const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
+        const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
+        if (e < ncs && u1 < sh1.ph && v1 < sh1.pw) {
+            const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
+            T z1, lu1, rn1, dl1;
+            proposal<T>(im, ch, m1, t0 + 1 + sw, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1], z1, lu1,
+                        rn1, dl1);
+            if (wide || lane == 0) {
+                T* pe = ring + ((size_t)q * kPropRing + (e & (kPropRing - 1))) * 4;
+                pe[0] = z1; pe[1] = lu1; pe[2] = rn1; pe[3] = dl1;
             }
         }
-    }
+    };
+    if (ahead && in_team && twarp == pwarp && g < npt) draw_ahead(g, 0);
     __syncthreads();
 
     for (int s = 0; s < nsteps; ++s) {
@@ -526,10 +538,11 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // a2 + a4: proposal and prior change (own tile state only)
             if (active) {
                 if (ahead) {
-                    z = s_prop[cs & 1][g][0];
-                    lu = s_prop[cs & 1][g][1];
-                    r_new = s_prop[cs & 1][g][2];
-                    delta = s_prop[cs & 1][g][3];
+                    const T* pe = ring + ((size_t)q * kPropRing + (cs & (kPropRing - 1))) * 4;
+                    z = pe[0];
+                    lu = pe[1];
+                    r_new = pe[2];
+                    delta = pe[3];
                 } else {
                     r_old = RES ? rho_s[(size_t)q * S2 + u * S + v] : rho_g[m];
                     proposal<T>(im, ch, m, t, r_old, z, lu, r_new, delta);
@@ -590,22 +603,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             if (active) decide();
             // the next step's draw, after the step barrier so that the other warps
             // need not wait for it there; it overlaps the neighbour wait below
-            if (ahead && in_team && twarp == pwarp && q < npt && cs + 1 < ncs) {
-                const int s1 = cs + 1, c1 = s1 % S2;
-                const int u1 = c1 / S, v1 = c1 - (c1 / S) * S;
-                const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
-                const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
-                if (u1 < sh1.ph && v1 < sh1.pw) {
-                    const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
-                    T z1, lu1, rn1, dl1;
-                    proposal<T>(im, ch, m1, t0 + 1 + s1 / S2, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1],
-                                z1, lu1, rn1, dl1);
-                    if (lane == 0) {
-                        s_prop[s1 & 1][g][0] = z1; s_prop[s1 & 1][g][1] = lu1;
-                        s_prop[s1 & 1][g][2] = rn1; s_prop[s1 & 1][g][3] = dl1;
-                    }
-                }
-            }
+            if (ahead && in_team && twarp == pwarp && q < npt && (!wide || (cs & (kPropRing - 1)) == kPropRing - 1))
+                draw_ahead(q, cs + 1);
             if (r == 0 && s > 0 && tid < 32) {
                 // stale: a neighbour changed data this window reads at its step s-1
                 // (or at step s, whose windows are disjoint from this one: a
