@@ -129,12 +129,11 @@ struct SmemPlan {
     size_t red, K, tw, ekl, ewa, em, prop, spec, rho, dat, total;
 };
 
-// Proposal ring of a sweep block whose teams each update one patch (tiles of
-// at most 8 patches): per patch, the draws (s_m z, log u, rho', delta) of the
-// next kPropRing class steps, made together by the lanes of one warp.
+// Proposal ring of a sweep block: per update team, the draws (s_m z, log u,
+// rho', delta) of its next kPropRing updates, made ahead by one warp.
 constexpr int kPropRing = 32;
 __host__ __device__ inline SmemPlan smem_plan(int L, int f, int S, int n_tw, int n_ent, int max_nhalf, int tpi,
-                                              int tpj, int resident, int tsize)
+                                              int tpj, int resident, int tsize, int teams)
 {
     SmemPlan p;
     size_t o = 0;
@@ -145,7 +144,7 @@ __host__ __device__ inline SmemPlan smem_plan(int L, int f, int S, int n_tw, int
     p.ekl = o; o += al16((size_t)4 * n_ent);
     p.ewa = o; o += al16((size_t)n_ent * tsize);
     p.em = o; o += al16((size_t)n_ent * tsize);
-    p.prop = o; o += al16(tpi * tpj <= 8 ? (size_t)tpi * tpj * kPropRing * 4 * tsize : 0);
+    p.prop = o; o += al16((size_t)teams * kPropRing * 4 * tsize);
     if (resident) {
         const int R = L / 2;
         // camera rows / columns seen by the tile's windows

@@ -305,14 +305,15 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     const int b_hi = !FINE ? min(W, j1) : min(W, (j1 - 1) / f + 1);
     const int rw = b_hi - b_lo;
 
-    const SmemPlan sp = smem_plan(L, f, S, im.n_tw, im.n_ent, im.max_nhalf, ch.tpi, ch.tpj, RES ? 1 : 0, sizeof(T));
+    const SmemPlan sp = smem_plan(L, f, S, im.n_tw, im.n_ent, im.max_nhalf, ch.tpi, ch.tpj, RES ? 1 : 0, sizeof(T),
+                                  max(1, (int)blockDim.x / im.team));
     T* red = reinterpret_cast<T*>(smem + sp.red);          // [2][8 sub-teams][8 warps][4]
     T* Ks = reinterpret_cast<T*>(smem + sp.K);
     T* tws = reinterpret_cast<T*>(smem + sp.tw);
     int* ekl = reinterpret_cast<int*>(smem + sp.ekl);
     T* ewa = reinterpret_cast<T*>(smem + sp.ewa);
     T* em = reinterpret_cast<T*>(smem + sp.em);
-    T* ring = reinterpret_cast<T*>(smem + sp.prop);         // [team][kPropRing][4] (one-patch teams)
+    T* ring = reinterpret_cast<T*>(smem + sp.prop);         // [team][kPropRing][4]
     T* spec_s = reinterpret_cast<T*>(smem + sp.spec);       // [npt][max_nhalf] complex
     T* rho_s = reinterpret_cast<T*>(smem + sp.rho);         // [npt][S*S]
     Dat4<T>* dat_s = reinterpret_cast<Dat4<T>*>(smem + sp.dat);
@@ -403,40 +404,46 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     const int nsw = ch.n_sweeps > 0 ? ch.n_sweeps : a.n_sweeps;
     const int nsteps = nsw * SS, ncs = nsw * S2;
     int n_acc = 0;
-    // with one update per team and step, a warp of the team draws the next
-    // step's proposal ahead of time, while the polling warp waits for the
-    // neighbours; not when a patch has a single class (S = 1), where the next
-    // step revisits the pixel
-    const bool ahead = rounds == 1 && S2 > 1 && ch.tpi * ch.tpj <= 8;   // (the ring exists for such tiles)
+    // a warp of each team draws the team's proposals ahead of time, between
+    // the step barriers (while the polling warp waits for the neighbours), into
+    // the ring.  Updates are numbered by round ordinal e = class step x rounds
+    // + round; the draw of update e uses the pixel's rho and scale, which
+    // change only at the pixel's own previous update, e - S^2 rounds, so a draw
+    // made fewer than S^2 rounds ahead is exact.  With more than kPropRing
+    // rounds per sweep the warp's lanes draw the next kPropRing updates
+    // together (wide), else the whole warp draws the next one.  Not when a
+    // sweep is a single round (S = 1 and one round), where the next update
+    // revisits the pixel.
+    const int SR = S2 * rounds;   // rounds per sweep
+    const bool ahead = SR > 1;
     const int pwarp = nwt > 1 ? 1 : 0;   // the drawing warp: not the one that polls the flags
     // one update per block and step (rounds == 1, n_sub == 1): a rejected
     // update scored on the neighbours' final state leaves nothing to write or
     // reread, so thread 0 publishes the step as soon as its wait ends
     // (s_pub: already published; thread 0 only)
-    // one-patch teams draw their proposals ahead: the drawing warp's lanes
-    // fill the ring kPropRing class steps at a time when a sweep has more than
-    // kPropRing classes (a pixel's rho and scale change only at its own update,
-    // once per sweep, so a draw made less than a sweep ahead gives the same
-    // move), else one step ahead (the whole warp on one draw)
-    const bool wide = ahead && S2 > kPropRing;
-    auto draw_ahead = [&](int q, int e0) {
-        const int e = e0 + (wide ? lane : 0);            // class-step ordinal of the draw
-        const int sw = e / S2, cl = e - sw * S2;
+    const bool wide = SR > kPropRing;
+    auto draw_ahead = [&](int e0) {
+        const int e = e0 + (wide ? lane : 0);            // round ordinal of the draw
+        const int cs_e = e / rounds, r_e = e - cs_e * rounds;
+        const int q = r_e * n_sub + g;                   // this team's patch in that round
+        const int sw = cs_e / S2, cl = cs_e - sw * S2;
         const int u1 = cl / S, v1 = cl - (cl / S) * S;
-        const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
-        const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
-        if (e < ncs && u1 < sh1.ph && v1 < sh1.pw) {
-            const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
-            T z1, lu1, rn1, dl1;
-            proposal<T>(im, ch, m1, t0 + 1 + sw, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1], z1, lu1,
-                        rn1, dl1);
-            if (wide || lane == 0) {
-                T* pe = ring + ((size_t)q * kPropRing + (e & (kPropRing - 1))) * 4;
-                pe[0] = z1; pe[1] = lu1; pe[2] = rn1; pe[3] = dl1;
+        if (cs_e < ncs && q < npt) {
+            const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
+            const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
+            if (u1 < sh1.ph && v1 < sh1.pw) {
+                const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
+                T z1, lu1, rn1, dl1;
+                proposal<T>(im, ch, m1, t0 + 1 + sw, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1], z1,
+                            lu1, rn1, dl1);
+                if (wide || lane == 0) {
+                    T* pe = ring + ((size_t)g * kPropRing + (e & (kPropRing - 1))) * 4;
+                    pe[0] = z1; pe[1] = lu1; pe[2] = rn1; pe[3] = dl1;
+                }
             }
         }
     };
-    if (ahead && in_team && twarp == pwarp && g < npt) draw_ahead(g, 0);
+    if (ahead && in_team && twarp == pwarp) draw_ahead(0);
     __syncthreads();
 
     for (int s = 0; s < nsteps; ++s) {
@@ -538,7 +545,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // a2 + a4: proposal and prior change (own tile state only)
             if (active) {
                 if (ahead) {
-                    const T* pe = ring + ((size_t)q * kPropRing + (cs & (kPropRing - 1))) * 4;
+                    const int e = cs * rounds + r;
+                    const T* pe = ring + ((size_t)g * kPropRing + (e & (kPropRing - 1))) * 4;
                     z = pe[0];
                     lu = pe[1];
                     r_new = pe[2];
@@ -603,8 +611,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             if (active) decide();
             // the next step's draw, after the step barrier so that the other warps
             // need not wait for it there; it overlaps the neighbour wait below
-            if (ahead && in_team && twarp == pwarp && q < npt && (!wide || (cs & (kPropRing - 1)) == kPropRing - 1))
-                draw_ahead(q, cs + 1);
+            if (ahead && in_team && twarp == pwarp) {
+                const int e = cs * rounds + r;
+                if (!wide || (e & (kPropRing - 1)) == kPropRing - 1) draw_ahead(e + 1);
+            }
             if (r == 0 && s > 0 && tid < 32) {
                 // stale: a neighbour changed data this window reads at its step s-1
                 // (or at step s, whose windows are disjoint from this one: a
