@@ -173,7 +173,7 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
     bool ok = true;
     word = 0;
     if (lane < nn) {
-        const int* f = prog + nbr[lane];
+        const int* f = prog + (size_t)nbr[lane] * kProgStride;
         // poll with relaxed loads (tight for the first polls, then with a short
         // sleep); the relaxed load that saw the step, followed by an acquire
         // fence, orders the reads of the neighbour's data after its release

@@ -74,7 +74,8 @@ struct Chain {
     double* trace_part;              // [slot][patch] accepted dL + dP
     unsigned long long* acc_count;   // [sweep - 1]
     uint8_t* acc_log;                // [sweep - 1][Ho*Wo] or null
-    int* prog;                       // per tile: progress word (steps published in this launch, change marks)
+    int* prog;                       // per tile, kProgStride ints apart: progress word (steps published in
+                                     // this launch, change marks)
     double* trace;                   // [sweep 0..max_sweeps]
     int tpi, tpj, nti, ntj;          // tile shape (patches) and tile grid
     int cta_base;                    // first block of this chain in the sweep grid
@@ -132,6 +133,11 @@ struct SmemPlan {
 // Proposal ring of a sweep block: per update team, the draws (s_m z, log u,
 // rho', delta) of its next kPropRing updates, made ahead by one warp.
 constexpr int kPropRing = 32;
+
+// Progress words are kProgStride ints apart (one 128-byte line per tile), so
+// that the neighbours' polls and the tile's publishes of different tiles do
+// not meet on the same L2 lines.
+constexpr int kProgStride = 32;
 __host__ __device__ inline SmemPlan smem_plan(int L, int f, int S, int n_tw, int n_ent, int max_nhalf, int tpi,
                                               int tpj, int resident, int tsize, int teams)
 {

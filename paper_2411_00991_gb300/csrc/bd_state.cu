@@ -374,7 +374,7 @@ __global__ void k_reset(const Image* imgs, const Chain* chains, int n_slots)
 {
     const Chain& ch = chains[blockIdx.x];
     const int np = imgs[ch.img].n_patches;
-    for (int k = threadIdx.x; k < np; k += blockDim.x) ch.prog[k] = 0;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) ch.prog[(size_t)k * kProgStride] = 0;
     for (int k = threadIdx.x; k < n_slots * np; k += blockDim.x) ch.trace_part[k] = 0.0;
 }
 

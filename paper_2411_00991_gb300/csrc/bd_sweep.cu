@@ -286,8 +286,21 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         s_ci = lo;
     }
     __syncthreads();
-    const Chain& ch = a.chains[s_ci];
-    const Image& im = a.imgs[ch.img];
+    // the chain and problem descriptors are copied to shared memory: the step
+    // loop reads them at every step, and after each neighbour wait's acquire
+    // fence they would otherwise be fetched from L2 again
+    __shared__ __align__(16) uint32_t s_chd[sizeof(Chain) / 4];
+    __shared__ __align__(16) uint32_t s_imd[sizeof(Image) / 4];
+    static_assert(sizeof(Chain) % 4 == 0 && sizeof(Image) % 4 == 0, "descriptor copies are whole words");
+    {
+        const uint32_t* gc = reinterpret_cast<const uint32_t*>(&a.chains[s_ci]);
+        const uint32_t* gi = reinterpret_cast<const uint32_t*>(&a.imgs[a.chains[s_ci].img]);
+        for (int k = tid; k < (int)(sizeof(Chain) / 4); k += blockDim.x) s_chd[k] = gc[k];
+        for (int k = tid; k < (int)(sizeof(Image) / 4); k += blockDim.x) s_imd[k] = gi[k];
+    }
+    __syncthreads();
+    const Chain& ch = *reinterpret_cast<const Chain*>(s_chd);
+    const Image& im = *reinterpret_cast<const Image*>(s_imd);
     const int t0 = *ch.tdev;          // sweeps completed before this launch (advanced after it by k_trace)
     const int tl = (int)blockIdx.x - ch.cta_base;
     const int ti = tl / ch.ntj, tj = tl - (tl / ch.ntj) * ch.ntj;
@@ -507,7 +520,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 if (tid == 0 && (int)blockIdx.x != a.silent_block) {
                     // the neighbours' next windows read these counts: mark the step
                     // changed (their speculative scores are redone) and release
-                    st_release(ch.prog + tl, prog_word(s + 1, true, s_chg != 0));
+                    st_release(ch.prog + (size_t)tl * kProgStride, prog_word(s + 1, true, s_chg != 0));
                     s_chg = 1;
                 }
                 continue;
@@ -628,7 +641,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     if (!ok) s_abort = 1;
                     s_stale = stale ? 1 : 0;
                     if (ok && !stale && !accept && rounds == 1 && n_sub == 1 && (int)blockIdx.x != a.silent_block) {
-                        st_relaxed(ch.prog + tl, prog_word(s + 1, false, s_chg != 0));
+                        st_relaxed(ch.prog + (size_t)tl * kProgStride, prog_word(s + 1, false, s_chg != 0));
                         s_chg = 0;
                         s_pub = 1;
                     }
@@ -744,10 +757,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 s_pub = 0;
             } else if (s_acc_any) {
                 s_acc_any = 0;
-                st_release(ch.prog + tl, prog_word(s + 1, true, s_chg != 0));
+                st_release(ch.prog + (size_t)tl * kProgStride, prog_word(s + 1, true, s_chg != 0));
                 s_chg = 1;
             } else {
-                st_relaxed(ch.prog + tl, prog_word(s + 1, false, s_chg != 0));
+                st_relaxed(ch.prog + (size_t)tl * kProgStride, prog_word(s + 1, false, s_chg != 0));
                 s_chg = 0;
             }
         }

@@ -496,7 +496,7 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
             x.o_tpart = A.take(8 * (size_t)kMaxSlots * ph.n_patches);
             x.o_acc = A.take(8 * (size_t)max_sweeps);
             x.o_log = (ph.p.flags & BDECON_FLAG_ACCEPT_LOG) ? A.take((size_t)max_sweeps * nobj) : 0;
-            x.o_prog = A.take(4 * (size_t)ph.n_patches);
+            x.o_prog = A.take(4 * (size_t)ph.n_patches * kProgStride);
             x.o_trace = A.take(8 * ((size_t)max_sweeps + 1));
             x.o_tdev = A.take(4);
             x.o_steps = adapt ? A.take(ts * nobj) : 0;
