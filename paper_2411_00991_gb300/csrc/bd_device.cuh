@@ -124,13 +124,18 @@ __device__ __forceinline__ T warp_sum(T v)
 }
 
 // ------------------------------------------------------ memory ordering --
-__device__ __forceinline__ void st_release(int* p, int v)
+// Fire-and-forget additions to a progress word.  Publishing by read-modify-
+// write keeps every word a reader can observe in observation order after the
+// tile's last release (PTX memory model: observation order runs through
+// atomic read-modify-writes, not plain stores), so a reader's acquire
+// synchronises with the tile's last change whatever later word it reads.
+__device__ __forceinline__ void red_add_release(int* p, int v)
 {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-__device__ __forceinline__ void st_relaxed(int* p, int v)
+__device__ __forceinline__ void red_add_relaxed(int* p, int v)
 {
-    asm volatile("st.relaxed.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_relaxed(const int* p)
 {
@@ -163,7 +168,9 @@ __device__ __forceinline__ int prog_word(int steps, bool changed, bool changed_b
 // lane) has published at least `need` steps.  Gives up (setting kErrTimeout)
 // after wait_ns nanoseconds (default 4 s) or 2^26 polls, or as soon as any
 // other block has raised an error.  Returns true if every flag arrived; word
-// receives the lane's neighbour word as the wait saw it.
+// receives the lane's neighbour word as the wait saw it (relaxed: the caller
+// follows the wait with fence_acq_rel_gpu, by every lane, where it reads
+// data the neighbours wrote).
 constexpr uint64_t kWaitNs = 4000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 26;
 __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr, int nn, int need,
@@ -175,8 +182,7 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
     if (lane < nn) {
         const int* f = prog + (size_t)nbr[lane] * kProgStride;
         // poll with relaxed loads (tight for the first polls, then with a short
-        // sleep); the relaxed load that saw the step, followed by an acquire
-        // fence, orders the reads of the neighbour's data after its release
+        // sleep)
         int v = ld_relaxed(f);
         if ((v >> 2) < need) {
             const uint64_t t0 = global_ns();
@@ -194,10 +200,7 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
                 if (it > 64u) __nanosleep(32);
             }
         }
-        if (ok) {
-            fence_acq_rel_gpu();
-            word = v;
-        }
+        if (ok) word = v;
     }
     return __all_sync(0xffffffffu, ok);
 }

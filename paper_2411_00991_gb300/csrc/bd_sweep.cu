@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     __shared__ int s_acc_any;
     __shared__ int s_pub;
     __shared__ int s_chg;   // the last published step changed data (thread 0 only)
+    __shared__ int s_word;  // the last published progress word (thread 0 only)
     __shared__ double s_phid[AUG ? 8 : 1][8];   // photon-count step: [sub-team][warp] log-density changes
     __shared__ __align__(8) uint64_t s_bar;      // completion of the tile's bulk copies (resident plans)
 
@@ -353,6 +354,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         s_acc_any = 0;
         s_pub = 0;
         s_chg = 0;
+        s_word = 0;
         if (RES) mbar_init(&s_bar, 1);
     }
     // Resident plans: the tile's per-pixel constants -- camera rows a_lo..a_hi-1,
@@ -471,6 +473,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 if (s > 0 && tid < 32) {
                     int word;
                     const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns, word);
+                    fence_acq_rel_gpu();
                     if (lane == 0 && !ok) s_abort = 1;
                 }
                 __syncthreads();
@@ -520,7 +523,9 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 if (tid == 0 && (int)blockIdx.x != a.silent_block) {
                     // the neighbours' next windows read these counts: mark the step
                     // changed (their speculative scores are redone) and release
-                    st_release(ch.prog + (size_t)tl * kProgStride, prog_word(s + 1, true, s_chg != 0));
+                    const int w = prog_word(s + 1, true, s_chg != 0);
+                    red_add_release(ch.prog + (size_t)tl * kProgStride, w - s_word);
+                    s_word = w;
                     s_chg = 1;
                 }
                 continue;
@@ -637,11 +642,19 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 bool stale = false;
                 if (ok && lane < s_nn) stale = (word & ((word >> 2) > s ? 3 : 1)) != 0;
                 stale = __any_sync(0xffffffffu, stale);
+                // acquire only when a neighbour changed data since this block's
+                // last acquire: otherwise nothing read after this wait was
+                // written by a neighbour since then (this step's reads came
+                // before the wait, and a neighbour's change at step s is marked
+                // in the words of the next wait)
+                if (stale) fence_acq_rel_gpu();
                 if (lane == 0) {
                     if (!ok) s_abort = 1;
                     s_stale = stale ? 1 : 0;
                     if (ok && !stale && !accept && rounds == 1 && n_sub == 1 && (int)blockIdx.x != a.silent_block) {
-                        st_relaxed(ch.prog + (size_t)tl * kProgStride, prog_word(s + 1, false, s_chg != 0));
+                        const int w = prog_word(s + 1, false, s_chg != 0);
+                        red_add_relaxed(ch.prog + (size_t)tl * kProgStride, w - s_word);
+                        s_word = w;
                         s_chg = 0;
                         s_pub = 1;
                     }
@@ -757,10 +770,14 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 s_pub = 0;
             } else if (s_acc_any) {
                 s_acc_any = 0;
-                st_release(ch.prog + (size_t)tl * kProgStride, prog_word(s + 1, true, s_chg != 0));
+                const int w = prog_word(s + 1, true, s_chg != 0);
+                red_add_release(ch.prog + (size_t)tl * kProgStride, w - s_word);
+                s_word = w;
                 s_chg = 1;
             } else {
-                st_relaxed(ch.prog + (size_t)tl * kProgStride, prog_word(s + 1, false, s_chg != 0));
+                const int w = prog_word(s + 1, false, s_chg != 0);
+                red_add_relaxed(ch.prog + (size_t)tl * kProgStride, w - s_word);
+                s_word = w;
                 s_chg = 0;
             }
         }
