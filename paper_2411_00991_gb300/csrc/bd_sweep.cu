@@ -257,7 +257,9 @@ __device__ __forceinline__ void lik_partial_aug(const T* mu_g, const T* phi_g, c
     }
 }
 
-template <typename T, bool RES, bool AUG, bool FINE>
+// SOLO: a form compiled for plans in which every block updates one patch with
+// one team (one round per step), without the multi-patch and multi-team paths
+template <typename T, bool RES, bool AUG, bool FINE, bool SOLO = false>
 __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_sweep(SweepArgs a)
 {
     using P = Prec<T>;
@@ -308,9 +310,9 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     const int S = im.S, L = im.L, R = im.R, H = im.H, W = im.W, S2 = S * S;
     // lattice f times finer than the camera (FINE; f = 1 otherwise): LL window cells per update
     const int f = FINE ? im.f : 1, Le = FINE ? im.Le : L, Lc = FINE ? im.Lc : L, LL = Lc * Lc;
-    const int pi0 = ti * ch.tpi, pj0 = tj * ch.tpj;
-    const int pi1 = min(pi0 + ch.tpi, im.npi), pj1 = min(pj0 + ch.tpj, im.npj);
-    const int tw_ = pj1 - pj0, npt = (pi1 - pi0) * tw_;
+    const int pi0 = SOLO ? ti : ti * ch.tpi, pj0 = SOLO ? tj : tj * ch.tpj;
+    const int pi1 = SOLO ? pi0 + 1 : min(pi0 + ch.tpi, im.npi), pj1 = SOLO ? pj0 + 1 : min(pj0 + ch.tpj, im.npj);
+    const int tw_ = SOLO ? 1 : pj1 - pj0, npt = SOLO ? 1 : (pi1 - pi0) * tw_;
     // camera region seen by the tile's windows
     const int i0 = pi0 * S, j0 = pj0 * S, i1 = min(pi1 * S, im.Ho), j1 = min(pj1 * S, im.Wo);
     const int a_lo = !FINE ? max(0, i0 - 2 * R) : max(0, i0 / f - (Lc - 1));
@@ -406,11 +408,11 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     }
 
     const int NT = im.team;
-    const int n_sub = max(1, (int)blockDim.x / NT);
-    const int g = tid / NT, lt = tid - (tid / NT) * NT;
-    const bool in_team = g < n_sub;
+    const int n_sub = SOLO ? 1 : max(1, (int)blockDim.x / NT);
+    const int g = SOLO ? 0 : tid / NT, lt = SOLO ? tid : tid - (tid / NT) * NT;
+    const bool in_team = SOLO || g < n_sub;
     const int twarp = lt >> 5, lane = tid & 31, nwt = NT >> 5;
-    const int rounds = (npt + n_sub - 1) / n_sub;
+    const int rounds = SOLO ? 1 : (npt + n_sub - 1) / n_sub;
     T* red1 = red + (size_t)(g * 8) * 4;                   // prior partials of this sub-team
     T* red2 = red + 8 * 8 * 4 + (size_t)(g * 8) * 4;       // likelihood partials
     // a sweep is S2 class steps, preceded in the augmented sampler by a
@@ -796,8 +798,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
 // The sweep kernel's form: tile state resident in shared memory or not,
 // augmented sampler or not, object lattice finer than the camera or not.
 template <typename T>
-const void* sweep_fn(bool res, bool aug, bool fine)
+const void* sweep_fn(bool res, bool aug, bool fine, bool solo)
 {
+    if constexpr (std::is_same<T, float>::value)
+        if (solo && res && !aug && !fine) return (const void*)k_sweep<T, true, false, false, true>;
     if (fine) {
         if (aug) return res ? (const void*)k_sweep<T, true, true, true> : (const void*)k_sweep<T, false, true, true>;
         return res ? (const void*)k_sweep<T, true, false, true> : (const void*)k_sweep<T, false, false, true>;
@@ -809,15 +813,16 @@ const void* sweep_fn(bool res, bool aug, bool fine)
 // Raise a kernel form's dynamic shared-memory limit to at least smem (the
 // limit only grows, so launches with smaller plans stay valid).
 template <typename T>
-cudaError_t ensure_smem_limit(bool res, bool aug, bool fine, size_t smem)
+cudaError_t ensure_smem_limit(bool res, bool aug, bool fine, bool solo, size_t smem)
 {
-    static std::atomic<size_t> limit[8];
+    static std::atomic<size_t> limit[16];
     static std::mutex mu;
-    const int form = (res ? 1 : 0) | (aug ? 2 : 0) | (fine ? 4 : 0);
+    const int form = (res ? 1 : 0) | (aug ? 2 : 0) | (fine ? 4 : 0) | (solo ? 8 : 0);
     if (limit[form].load() >= smem) return cudaSuccess;
     std::lock_guard<std::mutex> lock(mu);
     if (limit[form].load() >= smem) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(sweep_fn<T>(res, aug, fine), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(sweep_fn<T>(res, aug, fine, solo), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
     if (e == cudaSuccess) limit[form].store(smem);
     return e;
 }
@@ -830,8 +835,8 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
 {
     SweepArgs args = a;
     void* kargs[] = {&args};
-    const void* fn = sweep_fn<T>(a.resident, a.aug, a.fine);
-    cudaError_t e = ensure_smem_limit<T>(a.resident, a.aug, a.fine, smem);
+    const void* fn = sweep_fn<T>(a.resident, a.aug, a.fine, a.solo);
+    cudaError_t e = ensure_smem_limit<T>(a.resident, a.aug, a.fine, a.solo, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -852,13 +857,15 @@ template <typename T>
 int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine)
 {
     int best = 1 << 30;
-    for (int res = 0; res <= 1; ++res) {
+    for (int form = 0; form < 4; ++form) {   // resident or not, x one-team form or not
+        const bool res = (form & 1) != 0, solo = (form & 2) != 0;
         int n = 0;
-        if (ensure_smem_limit<T>(res != 0, aug, fine, smem) != cudaSuccess) {
+        if (ensure_smem_limit<T>(res, aug, fine, solo, smem) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_fn<T>(res != 0, aug, fine), threads, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_fn<T>(res, aug, fine, solo), threads, smem) !=
+            cudaSuccess)
             return 0;
         best = n < best ? n : best;
     }

@@ -65,6 +65,7 @@ struct Group {
     bool streamed = false;             // plan with tile state in global memory even if it fits in shared
     bool aug = false;                  // photon-count augmented problems (their own kernel form)
     bool fine = false;                 // object lattices finer than the camera (their own kernel form)
+    bool solo = false;                 // every block: one patch, one team (a kernel form of its own)
     int chain_off = 0, n_chains = 0;   // slice of the group-ordered chain table
 };
 
@@ -357,6 +358,8 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
         err = buf;
         return false;
     }
+    g.solo = true;
+    for (const PlanItem* it : items) g.solo = g.solo && it->tpi == 1 && it->tpj == 1 && g.threads == it->team;
     int base = 0;
     for (PlanItem* it : items) {
         const int nti = (it->ph->npi + it->tpi - 1) / it->tpi, ntj = (it->ph->npj + it->tpj - 1) / it->tpj;
@@ -839,6 +842,7 @@ bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle
         a.wait_ns = eh->wait_ns; a.silent_block = gi == 0 ? eh->silent_block : -1;
         a.aug = g.aug ? 1 : 0;
         a.fine = g.fine ? 1 : 0;
+        a.solo = g.solo ? 1 : 0;
         cudaError_t e = eh->precision == BDECON_FP32 ? launch_sweep<float>(a, g.grid, g.threads, g.smem, st)
                                                      : launch_sweep<double>(a, g.grid, g.threads, g.smem, st);
         if (e != cudaSuccess)
