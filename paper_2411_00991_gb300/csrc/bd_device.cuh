@@ -170,11 +170,12 @@ __device__ __forceinline__ int prog_word(int steps, bool changed, bool changed_b
 // other block has raised an error.  Returns true if every flag arrived; word
 // receives the lane's neighbour word as the wait saw it (relaxed: the caller
 // follows the wait with fence_acq_rel_gpu, by every lane, where it reads
-// data the neighbours wrote).
+// data the neighbours wrote).  pre: the word as this lane read it earlier
+// (relaxed), 0 if none; when it already shows the step, no load is issued.
 constexpr uint64_t kWaitNs = 4000000000ull;
 constexpr uint32_t kWaitPolls = 1u << 26;
 __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr, int nn, int need,
-                                                int* err, uint64_t wait_ns, int& word)
+                                                int* err, uint64_t wait_ns, int& word, int pre = 0)
 {
     const int lane = threadIdx.x & 31;
     bool ok = true;
@@ -183,7 +184,8 @@ __device__ __forceinline__ bool warp_wait_flags(const int* prog, const int* nbr,
         const int* f = prog + (size_t)nbr[lane] * kProgStride;
         // poll with relaxed loads (tight for the first polls, then with a short
         // sleep)
-        int v = ld_relaxed(f);
+        int v = pre;
+        if ((v >> 2) < need) v = ld_relaxed(f);
         if ((v >> 2) < need) {
             const uint64_t t0 = global_ns();
             uint32_t it = 0;

@@ -536,6 +536,14 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         const int c = AUG ? cc - 1 : cc;
         const int cs = slot * S2 + c;            // class-step ordinal
         const int u = c / S, v = c - (c / S) * S;
+        // one-team form: the polling warp reads the neighbours' progress words
+        // at the start of the step, so that the load overlaps the step's own
+        // work; the wait polls again only if a neighbour had not yet published
+        // the previous step (words only grow, and carry the change marks)
+        int pre = 0;
+        if constexpr (SOLO) {
+            if (s > 0 && tid < 32 && lane < s_nn) pre = ld_relaxed(ch.prog + (size_t)s_nbr[lane] * kProgStride);
+        }
         for (int r = 0; r < rounds; ++r) {
             const int q = r * n_sub + g;
             bool active = in_team && q < npt;
@@ -640,7 +648,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 // (or at step s, whose windows are disjoint from this one: a
                 // harmless recompute), read from the word the wait ended on
                 int word;
-                const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns, word);
+                const bool ok = warp_wait_flags(ch.prog, s_nbr, s_nn, s, a.err, a.wait_ns, word, pre);
                 bool stale = false;
                 if (ok && lane < s_nn) stale = (word & ((word >> 2) > s ? 3 : 1)) != 0;
                 stale = __any_sync(0xffffffffu, stale);
