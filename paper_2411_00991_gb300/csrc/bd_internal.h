@@ -98,7 +98,8 @@ struct SweepArgs {
     unsigned long long wait_ns;      // limit of each neighbour wait
     int silent_block;                // test knob: this block never publishes progress (-1: none)
     int solo;                        // every block updates one patch with one team (tiles of one patch,
-                                     // block = team): the float kernel has a form compiled for this plan
+                                     // block = team): the float resident camera-grid kernel (marginal and
+                                     // augmented) has a form compiled for this plan
 };
 
 // Threads that cooperate on one pixel update, sized by the PSF side: one warp

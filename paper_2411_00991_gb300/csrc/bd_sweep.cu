@@ -809,7 +809,8 @@ template <typename T>
 const void* sweep_fn(bool res, bool aug, bool fine, bool solo)
 {
     if constexpr (std::is_same<T, float>::value)
-        if (solo && res && !aug && !fine) return (const void*)k_sweep<T, true, false, false, true>;
+        if (solo && res && !fine)
+            return aug ? (const void*)k_sweep<T, true, true, false, true> : (const void*)k_sweep<T, true, false, false, true>;
     if (fine) {
         if (aug) return res ? (const void*)k_sweep<T, true, true, true> : (const void*)k_sweep<T, false, true, true>;
         return res ? (const void*)k_sweep<T, true, false, true> : (const void*)k_sweep<T, false, false, true>;
