@@ -192,7 +192,7 @@ template <typename T>
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 template <typename T>
 int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine);
-// zero every chain's progress words, last-accept words and trace partials
+// zero every chain's progress words and trace partials
 void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_slots, cudaStream_t st,
                   int64_t* launches);
 void launch_trace(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_sweeps,

@@ -772,10 +772,11 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         }
         if (tid == 0 && (int)blockIdx.x != a.silent_block) {
             // publish the step count with this step's and the previous step's
-            // change marks (read by the neighbours' staleness check); a step
-            // without an accepted update wrote nothing the neighbours read, and
-            // its own reads were consumed before the barrier, so a plain store
-            // suffices; otherwise release the mu writes
+            // change marks (read by the neighbours' staleness check), unless the
+            // step was published right after its wait (s_pub).  A step without an
+            // accepted update wrote nothing the neighbours read, and its own
+            // reads were consumed before the barrier, so a relaxed addition
+            // suffices; otherwise the addition releases the mu writes
             if (s_pub) {
                 s_pub = 0;
             } else if (s_acc_any) {
