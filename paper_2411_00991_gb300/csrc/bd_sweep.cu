@@ -136,11 +136,29 @@ __device__ __forceinline__ void window_fetch(const T* mu_g, const float4* cum_g,
                                              float4 (&cq)[kMaxPx], float2 (&cq2)[kMaxPx], int k0)
 {
     const int NT = im.team;
+    // camera grid: the cell's row and column (k / L, k mod L) are advanced
+    // from cell to cell (steps of NT) instead of divided out for each
+    const int L = im.L;
+    int kr = FINE ? 0 : k0 / L, kc = FINE ? 0 : k0 - kr * L;
+    const int dr = FINE ? 0 : NT / L, dc = FINE ? 0 : NT - dr * L;
 #pragma unroll
     for (int jj = 0; jj < kMaxPx; ++jj) {
         const int k = k0 + jj * NT;
         int aa, bb, kw;
-        const bool in = win_cell<FINE>(im, i, j, k, aa, bb, kw);
+        bool in;
+        if constexpr (FINE) {
+            in = win_cell<FINE>(im, i, j, k, aa, bb, kw);
+        } else {
+            aa = i - 2 * im.R + kr;
+            bb = j - 2 * im.R + kc;
+            in = k < L * L && (unsigned)aa < (unsigned)im.H && (unsigned)bb < (unsigned)im.W;
+            kc += dc;
+            kr += dr;
+            if (kc >= L) {
+                kc -= L;
+                ++kr;
+            }
+        }
         muv[jj] = in ? __ldcg(mu_g + (size_t)aa * im.mu_pitch + bb) : (T)-1;
         if (CUM) {
             cq[jj] = in ? __ldcg(cum_g + (size_t)aa * im.mu_pitch + bb) : make_float4(0, 0, 0, 0);
@@ -672,7 +690,15 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             }
             // (the partial sums are not read after this barrier, so the next round
             // may overwrite them; writes of an accepted update need one more)
-            const int any_accept = __syncthreads_or(active && accept ? 1 : 0);
+            // (one-team form: every thread took the same decision, so a plain
+            // barrier does)
+            int any_accept;
+            if constexpr (SOLO) {
+                __syncthreads();
+                any_accept = active && accept ? 1 : 0;
+            } else {
+                any_accept = __syncthreads_or(active && accept ? 1 : 0);
+            }
             if (s_abort) return;
             const bool stale = r == 0 && s > 0 && s_stale;
             if (stale) {
