@@ -164,45 +164,53 @@ def test_resume_from_checkpoint_is_exact():
         x.close()
 
 
-@pytest.mark.parametrize("precision", [bdecon.BDECON_FP64, bdecon.BDECON_FP32])
-def test_widefield512_first_class_sampled(precision):
-    # full 512x512 frame, L = 17, in the launch plan the benchmark uses: after
-    # one sweep the first-class pixels hold exactly the result of their single
-    # update from the initial object, which the oracle evaluates one by one
-    prob = synth.widefield_512()
+@pytest.mark.parametrize("frame,chains,precision", [
+    ("widefield_512", (0,), bdecon.BDECON_FP64),
+    ("widefield_512", (0,), bdecon.BDECON_FP32),
+    ("lowsnr_2048", (0, 3), bdecon.BDECON_FP64),
+])
+def test_full_frame_first_class_sampled(frame, chains, precision):
+    # full-size frames in the launch plan a user gets: the 512x512 widefield
+    # frame (L = 17, 1 chain) and the 2048x2048 low-SNR frame (L = 31, sCMOS
+    # maps, 4 chains).  After one sweep the first-class pixels hold exactly
+    # the result of their single update from the initial object, which the
+    # oracle evaluates one by one
+    prob = getattr(synth, frame)()
     s = bdecon.Sampler(prob, precision=precision, max_sweeps=4, flags=bdecon.FLAG_ACCEPT_LOG)
-    rho0, _ = s.get_state()
-    orc = O.Oracle(prob)
-    ref0 = orc.init()
-    if precision == bdecon.BDECON_FP64:
-        np.testing.assert_allclose(rho0, ref0, rtol=RTOL)
+    refs = {}
+    for c in chains:
+        orc = O.Oracle(prob, chain=c)
+        refs[c] = (orc, orc.init())
+        if precision == bdecon.BDECON_FP64:
+            np.testing.assert_allclose(s.get_state(0, c)[0], refs[c][1], rtol=RTOL)
     s.sweep(1)
-    rho1, _ = s.get_state()
-    acc = s.accept_log()[0]
     S = prob.S
     Ho, Wo = prob.object_shape()
-    rng = np.random.default_rng(3)
-    picks = [(0, 0), (Ho - 1 - (Ho - 1) % S, Wo - 1 - (Wo - 1) % S)] + \
-        [(int(a) * S, int(b) * S) for a, b in zip(rng.integers(0, (Ho - 1) // S + 1, 14),
-                                                   rng.integers(0, (Wo - 1) // S + 1, 14))]
-    near = 0
-    for i, j in picks:
-        m = i * Wo + j
-        a_o, rn, dl, dp = orc.single_update(ref0, m, 1)
-        if precision == bdecon.BDECON_FP64:
-            assert bool(acc[i, j]) == a_o
-            np.testing.assert_allclose(rho1[i, j], rn if a_o else ref0[i, j], rtol=1e-12)
-        else:
-            z, u = O.draw(prob.seed, m, 1, 0)
-            margin = abs(math.log(u) - (dl + dp + prob.step * z))
-            if margin > 1e-3:
+    for c in chains:
+        orc, ref0 = refs[c]
+        rho1, _ = s.get_state(0, c)
+        acc = s.accept_log(0, c)[0]
+        rng = np.random.default_rng(3 + c)
+        picks = [(0, 0), (Ho - 1 - (Ho - 1) % S, Wo - 1 - (Wo - 1) % S)] + \
+            [(int(a) * S, int(b) * S) for a, b in zip(rng.integers(0, (Ho - 1) // S + 1, 14),
+                                                       rng.integers(0, (Wo - 1) // S + 1, 14))]
+        near = 0
+        for i, j in picks:
+            m = i * Wo + j
+            a_o, rn, dl, dp = orc.single_update(ref0, m, 1)
+            if precision == bdecon.BDECON_FP64:
                 assert bool(acc[i, j]) == a_o
-                np.testing.assert_allclose(rho1[i, j], rn if a_o else ref0[i, j], rtol=2e-6)
+                np.testing.assert_allclose(rho1[i, j], rn if a_o else ref0[i, j], rtol=1e-12)
             else:
-                near += 1
-    assert near <= 2
-    tr = s.trace()
-    assert np.isfinite(tr).all()
+                z, u = O.draw(prob.seed, m, 1, c)
+                margin = abs(math.log(u) - (dl + dp + prob.step * z))
+                if margin > 1e-3:
+                    assert bool(acc[i, j]) == a_o
+                    np.testing.assert_allclose(rho1[i, j], rn if a_o else ref0[i, j], rtol=2e-6)
+                else:
+                    near += 1
+        assert near <= 2
+        assert np.isfinite(s.trace(0, c)).all()
     s.close()
 
 
@@ -304,3 +312,11 @@ def test_fp64_exact_chain_with_airy_psf():
     prob = synth.small_problem(H=30, W=26, L=13, maps=True, seed=19, refresh_every=6, burn_in=2)
     prob.psf = synth.airy_psf(1.4, 520.0, 65.0, 13)
     _compare_exact(prob, 15)
+
+
+@pytest.mark.xfail(reason="open defect: on the 2048x2048 low-SNR frame (L = 31, 4 chains, streamed "
+                          "multi-round float plan) three of four float chains report an infinite "
+                          "log-posterior trace after one sweep while their states stay finite; "
+                          "the 256x256 crop of the same frame is finite", strict=False)
+def test_lowsnr2048_float_first_class_sampled_and_trace():
+    test_full_frame_first_class_sampled("lowsnr_2048", (0, 3), bdecon.BDECON_FP32)
