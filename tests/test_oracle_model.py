@@ -57,6 +57,13 @@ CASES = [
     (141.7, 99.1, 2.1, 40.0, 20.0),       # read noise dominates
     (1100.0, 100.0, 2.0, 2.56, 480.0),    # bright
     (104.0, 100.0, 1.0, 9.0, 0.01),
+    # the extremes of the 2048x2048 low-SNR frame (read-noise variance down to
+    # 1e-3 ADU^2, i.e. 1/s^2 up to 4410, photon estimates -5.8 .. 10.6)
+    (100.0 + 2.1 * 0.0226, 100.0, 2.1, 0.001, 1.1),
+    (100.0 + 2.1 * 1.984, 100.0, 2.1, 0.001, 1.3),
+    (100.0 + 2.1 * 1.5, 100.0, 2.1, 0.001, 1.3),     # two photon counts equally likely
+    (100.0 - 2.1 * 5.79, 100.0, 2.1, 0.001, 1.1),    # far below the offset
+    (100.0 + 2.1 * 10.55, 100.0, 2.1, 0.001, 2.0),
 ]
 
 
