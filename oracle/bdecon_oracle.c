@@ -386,8 +386,9 @@ static double log_prior_all(const or_problem* P, const double* K, const double* 
     return tot;
 }
 
-/* Eq. 9: log posterior (up to the constant log B(alpha) terms) of rho. */
-double or_log_posterior(const or_problem* P, const double* rho)
+/* Likelihood part of Eq. 9: Eq. 6 summed over the camera pixels at the
+ * expected image of rho (Eq. 1-2).                                        */
+double or_log_likelihood(const or_problem* P, const double* rho)
 {
     const int H = P->H, W = P->W, L = P->L, f = sub_of(P), Le = L + f - 1;
     double* K = (double*)malloc((size_t)L * L * sizeof(double));
@@ -399,9 +400,18 @@ double or_log_posterior(const or_problem* P, const double* rho)
     double ll = 0.0;
     for (int n = 0; n < H * W; ++n)
         ll += or_loglik(P->w[n], P->offset[n], P->gain[n], P->var[n], mu[n]);
-    double lp = log_prior_all(P, K, rho);
     free(K); free(Ke); free(mu);
-    return ll + lp;
+    return ll;
+}
+
+/* Eq. 9: log posterior (up to the constant log B(alpha) terms) of rho. */
+double or_log_posterior(const or_problem* P, const double* rho)
+{
+    double* K = (double*)malloc((size_t)P->L * P->L * sizeof(double));
+    normalised_psf(P, K);
+    double lp = log_prior_all(P, K, rho);
+    free(K);
+    return or_log_likelihood(P, rho) + lp;
 }
 
 /* Log of the augmented joint density p(w, phi, rho) (prior without B(alpha)):

@@ -62,6 +62,8 @@ def lib():
         L.or_log_prior_patch.restype = C.c_double
         L.or_log_posterior.argtypes = [C.POINTER(OrProblem), C.c_void_p]
         L.or_log_posterior.restype = C.c_double
+        L.or_log_likelihood.argtypes = [C.POINTER(OrProblem), C.c_void_p]
+        L.or_log_likelihood.restype = C.c_double
         L.or_eff_kernel.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p]
         L.or_eff_kernel.restype = None
         L.or_expected.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
@@ -206,6 +208,30 @@ class Oracle:
         rho = np.ascontiguousarray(rho, dtype=np.float64)
         assert rho.shape == (self.Ho, self.Wo)
         return lib().or_log_posterior(C.byref(self.c), _p(rho))
+
+    def log_likelihood(self, rho: np.ndarray) -> float:
+        """Eq. 6 summed over the camera pixels at the expected image of rho."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        assert rho.shape == (self.Ho, self.Wo)
+        return lib().or_log_likelihood(C.byref(self.c), _p(rho))
+
+    def log_posterior_fft(self, rho: np.ndarray) -> float:
+        """Eq. 9 for large frames: the likelihood as in log_posterior, the patch
+        spectra of Eq. 8 taken by numpy's FFT (a library routine standing in
+        for the definitional DFT, which costs O(P^4) per patch) and passed to
+        the same patch log prior.  Equal to log_posterior up to rounding."""
+        rho = np.ascontiguousarray(rho, dtype=np.float64)
+        S = self.prob.S
+        alphas = {}
+        lp = 0.0
+        for i0 in range(0, self.Ho, S):
+            for j0 in range(0, self.Wo, S):
+                x = rho[i0:i0 + S, j0:j0 + S]
+                sh = x.shape
+                if sh not in alphas:
+                    alphas[sh] = alpha(self.psf / self.psf.sum(), sh[0], sh[1])
+                lp += log_prior_patch(np.fft.fft2(x), alphas[sh])
+        return self.log_likelihood(rho) + lp
 
     def init(self) -> np.ndarray:
         rho = np.empty((self.Ho, self.Wo))

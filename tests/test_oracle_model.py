@@ -238,3 +238,24 @@ def test_init_rule():
     for m in range(Ho * Wo):
         z, _ = O.draw(prob.seed, m, 0, 0)
         assert rho.flat[m] == pytest.approx(b0 * math.exp(0.1 * z), rel=1e-15)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(H=20, W=24, L=5, seed=7, maps=True),              # ragged patch tail, sCMOS maps
+    dict(H=16, W=19, L=5, stride=7, seed=9),               # stride > L, partial patches
+    dict(H=14, W=13, L=3, subpixel=2, seed=3),             # lattice finer than the camera
+])
+def test_fft_evaluator_equals_definitional_log_posterior(kw):
+    # the large-frame evaluator takes the patch spectra from numpy's FFT instead
+    # of the DFT written out by its definition; Eq. 9 must not change
+    prob = synth.small_problem(**kw)
+    orc = O.Oracle(prob)
+    rho = synth.random_state(prob, 11)
+    a, b = orc.log_posterior(rho), orc.log_posterior_fft(rho)
+    assert b == pytest.approx(a, rel=1e-12)
+    # and its likelihood part is Eq. 6 summed at the convolution of rho
+    mu = O.expected(rho, prob.H, prob.W, prob.psf / prob.psf.sum(), prob.subpixel)
+    g, o, v = prob.maps()
+    ll = sum(O.loglik(float(w), float(oo), float(gg), float(vv), float(m))
+             for w, oo, gg, vv, m in zip(prob.image.ravel(), o.ravel(), g.ravel(), v.ravel(), mu.ravel()))
+    assert orc.log_likelihood(rho) == pytest.approx(ll, rel=1e-12)
