@@ -42,6 +42,7 @@ template <typename T> struct Prec;
 template <> struct Prec<float> {
     static constexpr float kEps = 1.4901161193847656e-08f;  // 2^-26: sum truncation
     static constexpr float kMaxExp = 80.0f;
+    static constexpr float kMaxFinite = 3.4028234663852886e38f;
     static __device__ __forceinline__ float log(float x) { return logf(x); }
     static __device__ __forceinline__ float exp(float x) { return expf(x); }
     static __device__ __forceinline__ float log1p(float x) { return log1pf(x); }
@@ -65,6 +66,7 @@ template <> struct Prec<float> {
 template <> struct Prec<double> {
     static constexpr double kEps = 1.3877787807814457e-17;  // 2^-56
     static constexpr double kMaxExp = 700.0;
+    static constexpr double kMaxFinite = 1.7976931348623157e308;
     static __device__ __forceinline__ double log(double x) { return ::log(x); }
     static __device__ __forceinline__ double exp(double x) { return ::exp(x); }
     static __device__ __forceinline__ double log1p(double x) { return ::log1p(x); }

@@ -16,6 +16,7 @@ constexpr int kRedThreads = 256;    // fixed block size of every reduction
 // device error flag bits
 constexpr int kErrTimeout = 1;
 constexpr int kErrNumeric = 2;
+constexpr int kErrRatio = 4;        // a proposal's log acceptance ratio was not finite (record in err[1..9])
 
 // One patch shape (ph x pw) of a problem.  The prior of Eq. 8 is evaluated on
 // a canonical half of the frequencies: one representative of each Hermitian

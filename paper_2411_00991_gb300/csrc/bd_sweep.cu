@@ -43,6 +43,12 @@ namespace bd {
 // One entry of the patch prior change: X' = X + delta w, with
 //   |X'|^2 - |X|^2 = delta (2 Re(X conj w) + delta)        (|w| = 1)
 // accumulates  wa log(|X'|^2/|X|^2),  mult (|X'| - |X|),  mult |X|.
+// The ratio form q = (|X'|^2 - |X|^2)/|X|^2 is free of cancellation while
+// the coefficient does not shrink much (q > -1/2).  When it shrinks toward
+// zero, q rounds to -1 (log1p = -inf, and with wa < 0 an infinite gain that
+// the exact Eq. 7-8 change never has), so there the log is taken of the
+// ratio |X'|^2/|X|^2 itself, with X' the value an accepted update stores.
+// X' exactly 0 is rejected (the Dirichlet density is singular there).
 template <typename T>
 __device__ __forceinline__ void prior_term(T xr, T xi, T wr, T wi, T delta, T wa, T mult, T& accP, T& accS,
                                            T& accA, bool& bad)
@@ -54,9 +60,30 @@ __device__ __forceinline__ void prior_term(T xr, T xi, T wr, T wi, T delta, T wa
     const T n2n = rn * rn + in * in;
     if (!(n2n > (T)0)) bad = true;
     const T mo = P::sqrt(n2), mn = P::sqrt(n2n);
-    accP += wa * P::log1p(dd * P::rcp(n2));
+    const T i2 = P::rcp(n2);
+    const T q = dd * i2;
+    accP += wa * (q > (T)-0.5 ? P::log1p(q) : P::log(n2n * i2));
     accS += mult * (dd * P::rcp(mn + mo));
     accA += mult * mo;
+}
+
+// The target (Eq. 9) has a finite density at every state a chain can reach,
+// so a proposal whose log acceptance ratio is not finite (and that is not
+// impossible: mu' <= 0, a zero coefficient) is an arithmetic failure.  It is
+// rejected, the numeric error bit raised, and the first such update recorded
+// for the host: err[2] chain, err[3] pixel, err[8] sweep, dL and dP as
+// doubles at err + 4.
+__device__ __noinline__ void report_nonfinite(int* err, int chain, int m, int t, double dL, double dP)
+{
+    atomicOr(err, kErrRatio);
+    if (atomicCAS(err + 1, 0, 1) == 0) {
+        err[2] = chain;
+        err[3] = m;
+        err[8] = t;
+        double* d = reinterpret_cast<double*>(err + 4);
+        d[0] = dL;
+        d[1] = dP;
+    }
 }
 
 // x mod n for 0 <= x < 2^22 through a float reciprocal (exact after one correction)
@@ -638,7 +665,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // (the common case) leaves only the wait and the publish after it
             __syncthreads();
             T dL = 0, dP = 0;
-            bool accept = false;
+            bool accept = false, nonfin = false;
             auto decide = [&]() {
                 T sP = 0, sS = 0, sA = 0;
                 bool bad = false;
@@ -652,7 +679,9 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     bad = bad || red2[w * 4 + 1] != (T)0;
                 }
                 dP = sP + (T)(sh.K - 1) * P::log1p(sS / sA);
-                accept = !bad && (lu < dL + dP + z);   // z holds s_m z
+                const T tot = dL + dP;
+                nonfin = !bad && !(fabs(tot) <= (T)P::kMaxFinite);
+                accept = !bad && !nonfin && (lu < tot + z);   // z holds s_m z
             };
             if (active) decide();
             // the next step's draw, after the step barrier so that the other warps
@@ -713,6 +742,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 __syncthreads();
                 if (active) decide();
             }
+            if (active && nonfin && lt == 0) report_nonfinite(a.err, ch.chain, m, t, (double)dL, (double)dP);
             if (active) {
                 if (accept) {
                     const bool one_batch = LL <= NT * kMaxPx;

@@ -538,11 +538,20 @@ bdecon_status refresh(bdecon_handle* h, int ci, int write, double* out, const in
 
 bdecon_status check_device(bdecon_handle* h)
 {
-    int e = 0;
+    int e[10] = {};
     CK(h, cudaStreamSynchronize(h->st));
-    CK(h, cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e & kErrTimeout) { h->failed = true; return fail(h, BDECON_ERR_TIMEOUT, "a sub-lattice wait timed out on the device"); }
-    if (e & kErrNumeric) { h->failed = true; return fail(h, BDECON_ERR_NUMERIC, "non-finite or non-positive expected image"); }
+    CK(h, cudaMemcpy(e, h->d_err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e[0] & kErrTimeout) { h->failed = true; return fail(h, BDECON_ERR_TIMEOUT, "a sub-lattice wait timed out on the device"); }
+    if (e[0] & kErrNumeric) { h->failed = true; return fail(h, BDECON_ERR_NUMERIC, "non-finite or non-positive expected image"); }
+    if (e[0] & kErrRatio) {
+        double d[2];
+        std::memcpy(d, e + 4, sizeof d);
+        h->failed = true;
+        return fail(h, BDECON_ERR_NUMERIC,
+                    "non-finite log acceptance ratio (first: chain %d, object pixel %d, sweep %d, dL %g, dP %g); "
+                    "the update was rejected",
+                    e[2], e[3], e[8], d[0], d[1]);
+    }
     return BDECON_OK;
 }
 
@@ -1881,7 +1890,7 @@ void srv_loop(bdecon_server* S)
             const std::string m = S->shell.err;
             for (SrvJob* j : S->active) srv_finish(S, j, BDECON_JOB_FAILED, m);
             S->active.clear();
-            cudaMemsetAsync(S->shell.d_err, 0, sizeof(int), S->st);
+            cudaMemsetAsync(S->shell.d_err, 0, 64, S->st);   // flags and the first-event record
             S->shell.failed = false;
             dirty = true;
             continue;

@@ -31,7 +31,10 @@ def _collect(s, p, n_chains):
     out = []
     for c in range(n_chains):
         rho, t = s.get_state(p, c)
-        out.append((rho, s.trace(p, c), s.get_mu(p, c), s.accept_counts(p, c)))
+        tr = s.trace(p, c)
+        # equal traces compare equal even when infinite: check that they are finite
+        assert np.isfinite(tr).all() and np.isfinite(rho).all()
+        out.append((rho, tr, s.get_mu(p, c), s.accept_counts(p, c)))
     return out, s.posterior_mean(p)
 
 

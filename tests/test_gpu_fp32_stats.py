@@ -54,6 +54,41 @@ def test_fp32_trace_matches_oracle_posterior_of_its_state(refresh_every):
     s.close()
 
 
+@pytest.mark.parametrize("plan", [None, (6, 6, 0)])
+def test_widefield512_fp32_trace_matches_oracle_over_200_sweeps(plan):
+    # the 512x512 widefield frame (L = 17, 1 chain) at full size over many
+    # sweeps, in the plan a user gets -- one patch per block, one update team,
+    # the one-team kernel form -- and in a streamed multi-round plan (tiles of
+    # 6 x 6 patches, tile state in global memory, several rounds per class
+    # step); the trace at sweeps 50 (a refresh), 100 and 200 equals the
+    # oracle's Eq. 9 of the chain's state within 1e-5
+    prob = synth.widefield_512()
+    orc = O.Oracle(prob)
+    s = bdecon.Sampler(prob, precision=bdecon.BDECON_FP32, max_sweeps=200)
+    if plan is not None:
+        s.set_plan(*plan)
+    pl = s.get_plan(0)
+    if plan is None:
+        assert (pl["tile_i"], pl["tile_j"]) == (1, 1)
+    else:
+        assert (pl["tile_i"], pl["tile_j"]) == (6, 6)
+    done = 0
+    for t in (50, 100, 200):
+        s.sweep(t - done)
+        done = t
+        s.sync()
+        rho, tt = s.get_state()
+        assert tt == t
+        tr = s.trace()
+        assert np.isfinite(tr).all()
+        ref = orc.log_posterior_fft(rho)
+        print("plan %s sweep %d: trace %.10g oracle %.10g rel %.2e" % (pl, t, tr[t - 1], ref,
+                                                                       abs(tr[t - 1] - ref) / abs(ref)))
+        assert abs(tr[t - 1] - ref) <= TRACE_RTOL * abs(ref), (t, tr[t - 1], ref)
+    assert s.accept_counts().sum() > 10000
+    s.close()
+
+
 # ---------------------------------------------------------------- means
 H = W = 30
 LPSF = 3

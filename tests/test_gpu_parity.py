@@ -314,9 +314,8 @@ def test_fp64_exact_chain_with_airy_psf():
     _compare_exact(prob, 15)
 
 
-@pytest.mark.xfail(reason="open defect: on the 2048x2048 low-SNR frame (L = 31, 4 chains, streamed "
-                          "multi-round float plan) three of four float chains report an infinite "
-                          "log-posterior trace after one sweep while their states stay finite; "
-                          "the 256x256 crop of the same frame is finite", strict=False)
 def test_lowsnr2048_float_first_class_sampled_and_trace():
+    # the float form on the 2048x2048 low-SNR frame (L = 31, 4 chains, the
+    # streamed multi-round plan): sampled first-class updates match the
+    # oracle and every chain's trace is finite
     test_full_frame_first_class_sampled("lowsnr_2048", (0, 3), bdecon.BDECON_FP32)
