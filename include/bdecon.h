@@ -403,16 +403,24 @@ bdecon_status bdecon_server_stop(bdecon_server* s);
  * invalid values give a non-finite result.  Work is queued on stream
  * (cudaStream_t or NULL); the call returns without waiting.
  *
- * Scratch comes from one fixed array of 2^19 doubles (4 MiB) in the
- * library's device memory, held by every GPU that loads the library until
- * the process exits.  A problem needing more (L*L + 5*S*S + ceil(H*W/256) +
- * patches doubles; about 8 megapixel frames at most) is refused with
- * BDECON_ERR_INVALID and a message from bdecon_last_error(NULL).  The first
- * call on each device looks up the array's device address (once per
- * device, with that device current); make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents: calls whose work overlaps on the GPU (other streams, other host
- * threads) race on it and must be serialised by the caller.               */
+ * Scratch comes from one fixed array of 2^19 = 524288 doubles (4 MiB) in
+ * the library's device memory, held by every GPU that loads the library
+ * until the process exits.  A problem needs L*L + 5*S*S + ceil(H*W/256) +
+ * ceil((H+2R)/S)*ceil((W+2R)/S) doubles (S the stride, L when 0); one
+ * needing more than 2^19 is refused with BDECON_ERR_INVALID and a message
+ * from bdecon_last_error(NULL).  The limit therefore depends on the stride:
+ * about 32 megapixels at S = L = 9, 70 at S = L = 17, 4.5 at S = L = 3 and
+ * 0.5 at S = L = 1.  The first call on each device looks up the array's
+ * device address (once per device, with that device current).  Under the
+ * CUDA runtime's lazy module loading (the default) that first lookup may
+ * also load the library's device code and, with it, place the 4 MiB array:
+ * a one-time reservation made by the CUDA runtime, not by this call.  A
+ * caller that cannot allow even that while running makes one call during
+ * its set-up; that first call should also come before any stream capture.
+ * Later calls allocate nothing.  All calls share the array and it keeps
+ * the last call's contents (each call clears what it accumulates into):
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller.                         */
 bdecon_status bdecon_log_posterior_static(int32_t H, int32_t W, const float* image, int32_t L,
                                           const double* psf, const float* gain_map, double gain,
                                           const float* offset_map, double offset,

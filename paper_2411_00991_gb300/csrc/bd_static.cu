@@ -66,6 +66,7 @@ __device__ __forceinline__ void shape_sides(const StaticArgs& a, int s, int* ph,
 __global__ void __launch_bounds__(kRedThreads) k_static_alpha(StaticArgs a)
 {
     __shared__ double sh[kRedThreads];
+    __shared__ double2 eh[kMaxS], ew[kMaxS];
     double s = 0.0;
     for (int k = threadIdx.x; k < a.L * a.L; k += kRedThreads) s += a.psf[k];
     const double tot = sblock_sum(s, sh);
@@ -84,20 +85,32 @@ __global__ void __launch_bounds__(kRedThreads) k_static_alpha(StaticArgs a)
                     const int x = ((p - a.R) % ph + ph) % ph, y = ((q - a.R) % pw + pw) % pw;
                     a.kw[x * pw + y] += a.K[p * a.L + q];
                 }
+        // twiddles exp(-2 pi i j / ph) and exp(-2 pi i j / pw), as in k_static_prior
+        for (int j = threadIdx.x; j < ph; j += kRedThreads) {
+            double sn, cs;
+            sincospi(2.0 * (double)j / ph, &sn, &cs);
+            eh[j] = make_double2(cs, -sn);
+        }
+        for (int j = threadIdx.x; j < pw; j += kRedThreads) {
+            double sn, cs;
+            sincospi(2.0 * (double)j / pw, &sn, &cs);
+            ew[j] = make_double2(cs, -sn);
+        }
         __syncthreads();
         double part = 0.0;
         double* al = a.alpha + (size_t)sidx * a.S * a.S;
         for (int idx = threadIdx.x; idx < n; idx += kRedThreads) {
             const int k = idx / pw, l = idx % pw;
             double re = 0.0, im = 0.0;
-            for (int u = 0; u < ph; ++u)
+            for (int u = 0; u < ph; ++u) {
+                const double2 e1 = eh[(k * u) % ph];
                 for (int v = 0; v < pw; ++v) {
-                    const double fr = (double)((k * u) % ph) / ph + (double)((l * v) % pw) / pw;
-                    double sn, cs;
-                    sincospi(2.0 * fr, &sn, &cs);
-                    re += a.kw[u * pw + v] * cs;
-                    im -= a.kw[u * pw + v] * sn;
+                    const double2 e2 = ew[(l * v) % pw];
+                    const double x = a.kw[u * pw + v];
+                    re += x * (e1.x * e2.x - e1.y * e2.y);
+                    im += x * (e1.x * e2.y + e1.y * e2.x);
                 }
+            }
             al[idx] = hypot(re, im);
             part += al[idx];
         }

@@ -5,15 +5,18 @@ memory reserved up front for frame buffers, or a device allocator owned by
 another framework).  For them the library evaluates the log posterior of an
 object with its scratch in a fixed array inside the library.  These tests
 call it through the C ABI with device buffers the test itself allocated and
-compare it with the handle-based bdecon_log_posterior, at the 1e-12
-relative tolerance of the double-precision parity tests, on consecutive
-calls (the scratch keeps the previous call's contents).
+compare it with the handle-based bdecon_log_posterior and with the CPU
+oracle's Eq. 9, at the 1e-12 relative tolerance of the double-precision
+parity tests, on consecutive calls (the scratch keeps the previous call's
+contents), and check that warm calls leave the device's free memory
+unchanged.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2411_00991_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -73,6 +76,36 @@ def test_static_matches_handle_on_consecutive_calls():
     assert second == pytest.approx(ref_a, rel=RTOL)
     third = _static_value(b, rho_b, out)          # a smaller problem after a larger one
     assert third == pytest.approx(ref_b, rel=RTOL)
+    # the oracle's Eq. 9 of the same objects
+    assert first == pytest.approx(O.Oracle(a).log_posterior(rho_a), rel=RTOL)
+    assert third == pytest.approx(O.Oracle(b).log_posterior(rho_b), rel=RTOL)
+
+
+def test_static_warm_calls_leave_free_device_memory_unchanged():
+    # every device buffer is made before the measured calls, so only the
+    # entry point itself could change the device's free memory
+    a = synth.small_problem(H=33, W=30, L=5, maps=True, seed=33)
+    rho = synth.random_state(a, 6)
+    img, psf, r = _dev(a.image, torch.float32), _dev(a.psf, torch.float64), _dev(rho, torch.float64)
+    off, var = _dev(a.offset, torch.float32), _dev(a.var, torch.float32)
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+
+    def call(k):
+        bdecon.log_posterior_static(a.H, a.W, img.data_ptr(), a.L, psf.data_ptr(), float(a.gain),
+                                    ("map", off.data_ptr()), ("map", var.data_ptr()), a.stride, r.data_ptr(),
+                                    out[k:].data_ptr(), st)
+
+    call(0)                                       # set-up: the scratch address is looked up
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in (1, 2, 3):
+        call(k)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    v = out.cpu().numpy()
+    assert v[0] == pytest.approx(O.Oracle(a).log_posterior(rho), rel=RTOL)
+    assert (v[1:] == v[0]).all()
 
 
 def test_static_refuses_problems_beyond_its_scratch():
