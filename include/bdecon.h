@@ -148,8 +148,12 @@ bdecon_status bdecon_workspace_size(const bdecon_problem* problems, int32_t n_pr
  * On failure *out is NULL and nothing stays allocated.                     */
 bdecon_status bdecon_create(const bdecon_problem* problem, void* stream, bdecon_handle** out);
 
-/* Same for a batch of problems that share every launch (one persistent
- * sweep kernel covers all chains of all problems).                         */
+/* Same for a batch of problems of any sizes, PSFs and chain counts (one
+ * precision).  By default the problems are grouped by PSF side, stride and
+ * update team, and each group's chains run in one persistent cooperative
+ * launch of the sweep kernel per segment of sweeps (bdecon_set_grouping(h, 1)
+ * puts every problem in one launch; bdecon_autotune picks the faster).  A
+ * problem's results do not depend on the rest of the batch.               */
 bdecon_status bdecon_batch_create(const bdecon_problem* problems, int32_t n_problems,
                                   void* stream, bdecon_handle** out);
 
@@ -165,9 +169,14 @@ const char* bdecon_last_error(const bdecon_handle* h);
 
 /* --------------------------------------------------------------- sampling */
 
-/* Queue n sweeps of every chain (asynchronous on the handle's stream).  A
- * sweep visits the S*S sub-lattice classes in raster order of the in-patch
- * offset (u, v); every pixel of a class is updated once.  After sweep t the
+/* Queue n sweeps of every chain (asynchronous on the handle's stream): the
+ * paper's pixel-by-pixel sampler, each pixel drawn from its conditional
+ * given the rest of the object, with the pixels that are conditionally
+ * independent (windows beyond the PSF support) updated in parallel (Methods,
+ * "Parallelization Technique"; Fig. 5c-d).  Here each pixel update is one
+ * Metropolis-Hastings step with a log-space random walk.  A sweep visits the
+ * S*S sub-lattice classes in raster order of the in-patch offset (u, v);
+ * every pixel of a class is updated once.  After sweep t the
  * object is added to the running sum when t > burn_in, and mu, the patch
  * spectra and the log posterior are recomputed in double when t is a
  * multiple of refresh_every.  Errors: BDECON_ERR_STATE after a device
@@ -180,8 +189,10 @@ bdecon_status bdecon_sync(bdecon_handle* h);
 /* ---------------------------------------------------------------- results */
 
 /* Posterior mean of problem p over all its chains and all sweeps t >
- * burn_in so far, in double, into host out: (H+2R)*(W+2R) values, or the
- * H*W central crop when crop != 0.  BDECON_ERR_STATE if no sweep has been
+ * burn_in so far -- the paper's estimate of the object, the average of the
+ * sampled objects after burn-in (Results; the text after Eq. 9) -- in
+ * double, into host out: (H+2R)*(W+2R) values, or the H*W central crop when
+ * crop != 0.  BDECON_ERR_STATE if no sweep has been
  * averaged yet.                                                            */
 bdecon_status bdecon_posterior_mean(bdecon_handle* h, int32_t p, double* out, int32_t crop);
 
