@@ -318,6 +318,18 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
 bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int32_t* warps,
                               int32_t* tile_i, int32_t* tile_j);
 
+/* Window staging (float problems of the marginal sampler on the camera
+ * grid, PSF side <= 61): with enable = 1, plans other than the one-patch
+ * one-team form copy each update's expected-image and cumulant window -- the
+ * data the per-pixel update reads over the PSF window (Methods, Eq. 6;
+ * Fig. 5d) -- and, when tile state is streamed, its patch spectrum (Eq. 8)
+ * into shared memory with the TMA engine, the next update's copy in flight
+ * while the current one computes.  Its buffers lower the blocks per SM, so
+ * it is off by default and bdecon_autotune tries it.  Results do not change.
+ * bdecon_get_staging reports whether problem p's launch group is staged.   */
+bdecon_status bdecon_set_staging(bdecon_handle* h, int32_t enable);
+bdecon_status bdecon_get_staging(bdecon_handle* h, int32_t p, int32_t* staged);
+
 /* Kernel launches issued by this handle since creation.                    */
 bdecon_status bdecon_launch_count(const bdecon_handle* h, int64_t* launches);
 

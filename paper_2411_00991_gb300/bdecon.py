@@ -60,7 +60,7 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_server_submit", "bdecon_server_poll", "bdecon_server_wait", "bdecon_server_stats",
            "bdecon_server_stop", "bdecon_set_grouping", "bdecon_autotune", "bdecon_set_graph",
            "bdecon_posterior_std", "bdecon_posterior_cv", "bdecon_get_samples", "bdecon_posterior_quantiles",
-           "bdecon_get_steps", "bdecon_get_phi"]
+           "bdecon_get_steps", "bdecon_get_phi", "bdecon_set_staging", "bdecon_get_staging"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -107,6 +107,8 @@ def load(build_if_missing: bool = True):
         "bdecon_delta": [H, i32, i32, i64, C.c_double, dp, dp, C.POINTER(i32)],
         "bdecon_set_plan": [H, i32, i32, i32, i32],
         "bdecon_get_plan": [H, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)],
+        "bdecon_set_staging": [H, i32],
+        "bdecon_get_staging": [H, i32, C.POINTER(i32)],
         "bdecon_launch_count": [H, C.POINTER(i64)],
         "bdecon_set_timing": [H, i32],
         "bdecon_sweep_kernel_time": [H, dp, C.POINTER(i64)],
@@ -396,6 +398,15 @@ class Sampler:
         b, w, ti, tj = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         self._ck(self.L.bdecon_get_plan(self.h, p, C.byref(b), C.byref(w), C.byref(ti), C.byref(tj)))
         return dict(blocks=b.value, warps=w.value, tile_i=ti.value, tile_j=tj.value)
+
+    def set_staging(self, enable: bool = True):
+        self._ck(self.L.bdecon_set_staging(self.h, int(bool(enable))))
+
+    def staged(self, p: int = 0) -> int:
+        """1 when problem p's launch group runs with window staging, else 0."""
+        v = C.c_int32()
+        self._ck(self.L.bdecon_get_staging(self.h, p, C.byref(v)))
+        return int(v.value)
 
     def set_fault(self, silent_block: int, wait_ns: int = 4_000_000_000):
         self._ck(self.L.bdecon_set_fault(self.h, int(silent_block), int(wait_ns)))

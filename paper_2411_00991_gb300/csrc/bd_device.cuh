@@ -238,6 +238,26 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// Tiled 2-D copy of one box of a tensor (described by a TMA tensor map in
+// global memory, 64-byte aligned) at element coordinates (x, y) into shared
+// memory (128-byte aligned), completing on the mbarrier.  x times the
+// element size must be a multiple of 16 bytes; y may be negative or past the
+// end (those rows, like out-of-range columns, are filled with zeros).
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+// Orders this thread's earlier generic-proxy accesses to global memory (and
+// those made visible to it by barriers and acquire fences) before its later
+// async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
 {
     uint32_t done;

@@ -85,6 +85,8 @@ struct Chain {
     void* samples;                   // [n_samples][Ho*Wo] T kept objects, or null
     void* steps;                     // [Ho*Wo] T per-pixel proposal scales (adapting problems), or null
     void* phi;                       // [H*mu_pitch] T photon counts (augmented sampler), or null
+    const void* tmap;                // float marginal camera-grid chains: three 128-byte TMA tensor maps
+                                     // (mu, cumulants c1..c4, c5..c6) for window staging, or null
 };
 
 struct SweepArgs {
@@ -101,7 +103,47 @@ struct SweepArgs {
     int solo;                        // every block updates one patch with one team (tiles of one patch,
                                      // block = team): the float resident camera-grid kernel (marginal and
                                      // augmented) has a form compiled for this plan
+    int stage;                       // 1: window staging -- each update's expected-image and cumulant window
+                                     // (and, streamed, its patch spectrum) copied to shared memory by the TMA
+                                     // engine, the next round's while the current one computes; 0: none
 };
+
+// Window staging (float marginal sampler on the camera grid).  The window of
+// the update of object pixel (i, j) is the camera box rows i-2R..i, columns
+// j-2R..j; it is copied as a box of kStageW(L) columns starting at column
+// x0 = (j - 2R) rounded down to a multiple of 4 (a TMA copy must start on a
+// 16-byte boundary), L rows, from three tensors: mu (float), the cumulants
+// c1..c4 (float4 per pixel, 4 floats) and c5, c6 (float2, 2 floats).  Cells
+// outside the frame are filled with zeros (mu = 0 never occurs inside the
+// frame).  A box side is at most 256 elements, so staging needs
+// 4 kStageW(L) <= 256, i.e. L <= 61.
+constexpr int kStageMaxL = 61;
+__host__ __device__ inline int stage_w(int L) { return (L + 6) & ~3; }   // round_up_4(L + 3)
+__host__ __device__ inline size_t al128(size_t x) { return (x + 127) & ~(size_t)127; }
+struct StagePlan {
+    size_t mu, cum, cum2, spec, per_buf, bar;   // offsets within one buffer; bytes per buffer
+    uint32_t tx_win, tx_spec;                   // bytes each copy set delivers
+};
+// the window, and the spectrum when the tile state is not resident
+__host__ __device__ inline StagePlan stage_plan(int L, int max_nhalf, int mode, int resident)
+{
+    StagePlan p;
+    const size_t cells = mode == 1 ? (size_t)stage_w(L) * L : 0;
+    size_t o = 0;
+    p.mu = o; o += al128(4 * cells);
+    p.cum = o; o += al128(16 * cells);
+    p.cum2 = o; o += al128(8 * cells);
+    p.spec = o;
+    // the half spectrum, rounded up to an even number of complex floats (16 bytes)
+    const bool spec = mode == 1 && !resident;
+    const size_t spec_bytes = spec ? (size_t)((max_nhalf + 1) & ~1) * 8 : 0;
+    o += al128(spec_bytes);
+    p.per_buf = o;
+    p.tx_win = (uint32_t)(28 * cells);
+    p.tx_spec = (uint32_t)spec_bytes;
+    p.bar = 0;
+    return p;
+}
 
 // Threads that cooperate on one pixel update, sized by the PSF side: one warp
 // per 100 window pixels, 1..8 warps (at most 4 window pixels per thread up to
@@ -115,14 +157,18 @@ __host__ __device__ inline int team_threads(int L)
     return 32 * w;
 }
 
-// Team of a problem: the requested warps, else one warp when the problem
-// alone has many independent updates per class step (chains x patches >=
-// 2048: throughput comes from many updates in flight), else team_threads(L)
-// (few updates per step: latency comes from the length of each update).
-__host__ __device__ inline int problem_team(int L, int n_chains, int n_patches, int team_warps)
+// Team of a problem: the requested warps; else, when the problem alone has
+// many independent updates per class step (chains x patches >= 2048:
+// throughput comes from many updates in flight), a small team -- in float,
+// 1 warp up to 128 window pixels, 2 up to 600, 4 beyond (measured best on
+// the 64-frame batch and the 2048 x 2048 frame: larger windows are
+// latency-bound on one warp); in double 1 warp (the double sweep is bound by
+// its arithmetic); else team_threads(L) (few updates per step: latency comes
+// from the length of each update).
+__host__ __device__ inline int problem_team(int L, int n_chains, int n_patches, int team_warps, bool fp32)
 {
     if (team_warps > 0) return 32 * (team_warps > 8 ? 8 : team_warps);
-    if ((long long)n_chains * n_patches >= 2048) return 32;
+    if ((long long)n_chains * n_patches >= 2048) return !fp32 || L * L <= 128 ? 32 : L * L <= 600 ? 64 : 128;
     return team_threads(L);
 }
 
@@ -131,7 +177,7 @@ __host__ __device__ inline int problem_team(int L, int n_chains, int n_patches, 
 // spectra and its object values.
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 struct SmemPlan {
-    size_t red, K, tw, ekl, ewa, em, prop, spec, rho, dat, total;
+    size_t red, K, tw, ekl, ewa, em, prop, spec, rho, dat, stage, stage_bar, total;
 };
 
 // Proposal ring of a sweep block: per update team, the draws (s_m z, log u,
@@ -143,7 +189,7 @@ constexpr int kPropRing = 32;
 // not meet on the same L2 lines.
 constexpr int kProgStride = 32;
 __host__ __device__ inline SmemPlan smem_plan(int L, int f, int S, int n_tw, int n_ent, int max_nhalf, int tpi,
-                                              int tpj, int resident, int tsize, int teams)
+                                              int tpj, int resident, int tsize, int teams, int stage = 0)
 {
     SmemPlan p;
     size_t o = 0;
@@ -165,6 +211,16 @@ __host__ __device__ inline SmemPlan smem_plan(int L, int f, int S, int n_tw, int
         p.dat = o; o += al16((size_t)ch * cw * 4 * tsize);
     } else {
         p.spec = p.rho = p.dat = o;
+    }
+    p.stage = p.stage_bar = o;
+    if (stage) {
+        // per update team: two staging buffers (the current round's and the next
+        // one's) and their two completion barriers
+        o = al128(o);
+        p.stage = o;
+        o += (size_t)teams * 2 * stage_plan(L, max_nhalf, stage, resident).per_buf;
+        p.stage_bar = o;
+        o += al16((size_t)teams * 2 * 8);
     }
     p.total = o;
     return p;
@@ -192,7 +248,7 @@ void launch_sample_phi(const Image& im, const Chain& ch, int t, int* err, cudaSt
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 template <typename T>
-int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine);
+int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine, int stg);
 // zero every chain's progress words and trace partials
 void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_slots, cudaStream_t st,
                   int64_t* launches);

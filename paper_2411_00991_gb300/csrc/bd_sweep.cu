@@ -244,6 +244,54 @@ __device__ __forceinline__ void lik_partial(const T* mu_g, const float4* cum_g, 
     }
 }
 
+// Likelihood part of one update for one team thread from the staged window
+// (float marginal sampler, camera grid): the same cells in the same order
+// with the same arithmetic as lik_partial, the expected image and the
+// cumulants read from the shared-memory copy of the window (row stride BW,
+// column offset dx of the window's first column within the copied box;
+// cells outside the frame hold mu = 0).
+template <bool RES>
+__device__ __forceinline__ void lik_partial_staged(const float* wmu, const float4* wcum, const float2* wcum2, int BW,
+                                                   int dx, const Dat4<float>* dat_s, const Dat4<float>* dat_g,
+                                                   const float* Ks, const Image& im, int i, int j, int a_lo, int b_lo,
+                                                   int rw, int lt, int NT, float delta, float* out, int lane)
+{
+    const int W = im.W, L = im.L, LL = L * L, R2 = 2 * im.R;
+    float accL = 0.0f;
+    bool badL = false;
+    int kr = lt / L, kc = lt - (lt / L) * L;
+    const int dr = NT / L, dc = NT - (NT / L) * L;
+    for (int k = lt; k < LL; k += NT) {
+        const int sidx = kr * BW + dx + kc;
+        const float mu = wmu[sidx];
+        if (mu > 0.0f) {
+            const float xk = mul_rn(delta, Ks[k]);
+            const float d = xk * Prec<float>::rcp(mu);
+            if (fabsf(d) <= kCumEval) {
+                accL += cgf_delta(xk, log1p_cum(d), wcum[sidx], wcum2[sidx]);
+            } else {
+                const int aa = i - R2 + kr, bb = j - R2 + kc;
+                const Dat4<float> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
+                int b = 0;
+                accL += dl_pixel_call(mu, xk, dv.c, dv.is2, dv.beta, &b);
+                badL = badL || b;
+            }
+        }
+        kc += dc;
+        kr += dr;
+        if (kc >= L) {
+            kc -= L;
+            ++kr;
+        }
+    }
+    accL = warp_sum(accL);
+    const bool wb = __any_sync(0xffffffffu, badL);
+    if (lane == 0) {
+        out[0] = accL;
+        out[1] = wb ? 1.0f : 0.0f;
+    }
+}
+
 // Augmented sampler: the window's expected image and photon counts.
 template <typename T, bool FINE>
 __device__ __forceinline__ void window_fetch_aug(const T* mu_g, const T* phi_g, const Image& im, int i, int j,
@@ -304,14 +352,23 @@ __device__ __forceinline__ void lik_partial_aug(const T* mu_g, const T* phi_g, c
 
 // SOLO: a form compiled for plans in which every block updates one patch with
 // one team (one round per step), without the multi-patch and multi-team paths
-template <typename T, bool RES, bool AUG, bool FINE, bool SOLO = false>
+// STG: window staging (float marginal sampler on the camera grid, not the
+// one-team form): each update's expected-image and cumulant window -- and, in
+// streamed plans, its patch spectrum -- is copied into a shared-memory buffer
+// of its team by the TMA engine, the next round's copy in flight while the
+// current round computes (two buffers per team)
+template <typename T, bool RES, bool AUG, bool FINE, bool SOLO = false, int STG = 0>
 __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_sweep(SweepArgs a)
 {
     using P = Prec<T>;
     // float sweeps of the marginal sampler use the cumulant cache; the
     // augmented sampler (AUG) scores windows from the photon counts instead
     constexpr bool CUM = std::is_same<T, float>::value && !AUG;
-    extern __shared__ __align__(16) unsigned char smem[];
+    static_assert(STG == 0 || (std::is_same<T, float>::value && !AUG && !FINE && !SOLO), "staging: float marginal camera grid");
+    constexpr bool SANY = STG != 0;                          // staging
+    constexpr bool SWIN = STG == 1;                          // the window is staged
+    constexpr bool SSPEC = STG == 1 && !RES;                 // the patch spectrum is staged (streamed plans)
+    extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_nbr[8];
     __shared__ int s_nn;
     __shared__ int s_abort;
@@ -367,7 +424,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     const int rw = b_hi - b_lo;
 
     const SmemPlan sp = smem_plan(L, f, S, im.n_tw, im.n_ent, im.max_nhalf, ch.tpi, ch.tpj, RES ? 1 : 0, sizeof(T),
-                                  max(1, (int)blockDim.x / im.team));
+                                  max(1, (int)blockDim.x / im.team), STG);
+    const StagePlan stp = stage_plan(L, im.max_nhalf, STG, RES ? 1 : 0);
+    const int BW = stage_w(L);
+    uint64_t* stg_bar = reinterpret_cast<uint64_t*>(smem + sp.stage_bar);   // [team][buffer]
     T* red = reinterpret_cast<T*>(smem + sp.red);          // [2][8 sub-teams][8 warps][4]
     T* Ks = reinterpret_cast<T*>(smem + sp.K);
     T* tws = reinterpret_cast<T*>(smem + sp.tw);
@@ -403,6 +463,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
         s_chg = 0;
         s_word = 0;
         if (RES) mbar_init(&s_bar, 1);
+        if (SANY)
+            for (int k = 0; k < 2 * max(1, (int)blockDim.x / im.team); ++k) mbar_init(&stg_bar[k], 1);
     }
     // Resident plans: the tile's per-pixel constants -- camera rows a_lo..a_hi-1,
     // columns b_lo..b_hi-1, i.e. the tile's windows with the PSF halo -- are
@@ -505,6 +567,60 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             }
         }
     };
+    // Window staging (STG).  Round ordinal e of this team uses buffer e & 1;
+    // the copy set of round e + 1 is issued while round e computes, except
+    // that the first round of a class step is issued after the previous step's
+    // writes (its windows overlap them) and, like the register path's
+    // speculative fetch, is re-copied when the neighbour wait finds it stale.
+    // Issue and wait conditions are the same predicate, so each barrier's
+    // phases stay in step; stg_par holds the parity to wait for per buffer and
+    // stg_pend the buffers with a copy in flight (both uniform in a team).
+    uint32_t stg_par = 0, stg_pend = 0;
+    auto stg_buf = [&](int b) { return smem + sp.stage + ((size_t)g * 2 + b) * stp.per_buf; };
+    auto stage_issue = [&](int e) -> bool {
+        if (!SANY || !in_team) return false;
+        const int cs_e = e / rounds, r_e = e - cs_e * rounds;
+        const int q = r_e * n_sub + g;
+        if (cs_e >= ncs || q >= npt) return false;
+        const int cl = cs_e - (cs_e / S2) * S2;
+        const int u1 = cl / S, v1 = cl - (cl / S) * S;
+        const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
+        const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
+        if (u1 >= sh1.ph || v1 >= sh1.pw) return false;
+        const int b = e & 1;
+        if (lt == 0) {
+            unsigned char* buf = stg_buf(b);
+            uint64_t* bar = &stg_bar[g * 2 + b];
+            const int x0 = (pj_ * S + v1 - 2 * R) & ~3, y0 = pi_ * S + u1 - 2 * R;
+            const uint32_t spec_bytes = SSPEC ? (uint32_t)((sh1.nhalf + 1) & ~1) * 8u : 0u;
+            const char* tm = reinterpret_cast<const char*>(ch.tmap);
+            fence_proxy_async_global();
+            mbar_arrive_expect_tx(bar, (SWIN ? stp.tx_win : 0u) + spec_bytes);
+            if (SWIN) {
+                tma_load_2d(buf + stp.mu, tm, x0, y0, bar);
+                tma_load_2d(buf + stp.cum, tm + 128, 4 * x0, y0, bar);
+                tma_load_2d(buf + stp.cum2, tm + 256, 2 * x0, y0, bar);
+            }
+            if (SSPEC) bulk_g2s(buf + stp.spec, spec_g + 2 * im.patch_off[pi_ * im.npj + pj_], spec_bytes, bar);
+        }
+        stg_pend |= 1u << b;
+        return true;
+    };
+    auto stage_wait = [&](int b) {
+        const bool ok = mbar_wait(&stg_bar[g * 2 + b], (stg_par >> b) & 1u, a.wait_ns);
+        stg_par ^= 1u << b;
+        stg_pend &= ~(1u << b);
+        if (!ok) {
+            atomicOr(a.err, kErrTimeout);
+            s_abort = 1;
+        }
+    };
+    // before the block returns: copies still in flight must land first (bounded)
+    auto stage_drain = [&]() {
+        for (int b = 0; b < 2; ++b)
+            if ((stg_pend >> b) & 1u) stage_wait(b);
+    };
+    if (SANY) stage_issue(0);
     if (ahead && in_team && twarp == pwarp) draw_ahead(0);
     __syncthreads();
 
@@ -609,9 +725,23 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             float4 cq[AUG ? 1 : kMaxPx];
             float2 cq2[AUG ? 1 : kMaxPx];
             T phv[AUG ? kMaxPx : 1];
+            // staged window of this round (STG): buffer e & 1 of the team
+            const int e_cur = cs * rounds + r, sb = e_cur & 1;
+            const float* wmu = reinterpret_cast<const float*>(stg_buf(sb) + stp.mu);
+            const float4* wcum = reinterpret_cast<const float4*>(stg_buf(sb) + stp.cum);
+            const float2* wcum2 = reinterpret_cast<const float2*>(stg_buf(sb) + stp.cum2);
+            const int wdx = (j - 2 * R) - ((j - 2 * R) & ~3);
+            // spectrum read here (the staged copy in streamed STG plans); writes go to spec_p
+            const T* spec_rd = SSPEC ? reinterpret_cast<const T*>(stg_buf(sb) + stp.spec) : spec_p;
+            if constexpr (SANY) {
+                if (active) stage_wait(sb);
+                // the next round of this step: its window is disjoint from this one
+                // (same class, another patch), so its copy overlaps this round's work
+                if (r >= 1 && r + 1 < rounds) stage_issue(e_cur + 1);
+            }
             // the window's first batch is fetched before the prior work so its
             // latency overlaps the arithmetic below
-            if (active) {
+            if (active && !SWIN) {
                 if constexpr (AUG) window_fetch_aug<T, FINE>(mu_g, phi_g, im, i, j, muv, phv, lt);
                 else window_fetch<T, CUM, FINE>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, lt);
             }
@@ -633,7 +763,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     T wr, wi;
                     const int ent = sh.ent_off + e;
                     twiddle(tws, sh, ekl[ent], u, v, wr, wi);
-                    prior_term<T>(spec_p[2 * e], spec_p[2 * e + 1], wr, wi, delta, ewa[ent], em[ent], accP, accS,
+                    prior_term<T>(spec_rd[2 * e], spec_rd[2 * e + 1], wr, wi, delta, ewa[ent], em[ent], accP, accS,
                                   accA, badP);
                 }
                 accP = warp_sum(accP);
@@ -655,6 +785,9 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 if constexpr (AUG)
                     lik_partial_aug<T, FINE>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane,
                                              true);
+                else if constexpr (SWIN)
+                    lik_partial_staged<RES>(wmu, wcum, wcum2, BW, wdx, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt,
+                                            NT, delta, red2 + twarp * 4, lane);
                 else
                     lik_partial<T, RES, CUM, FINE>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
                                              delta, muv, red2 + twarp * 4, lane, cq, cq2, true);
@@ -728,20 +861,37 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             } else {
                 any_accept = __syncthreads_or(active && accept ? 1 : 0);
             }
-            if (s_abort) return;
+            if (s_abort) {
+                stage_drain();
+                return;
+            }
             const bool stale = r == 0 && s > 0 && s_stale;
             if (stale) {
                 if (active) {
-                    if constexpr (AUG)
+                    if constexpr (AUG) {
                         lik_partial_aug<T, FINE>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4,
                                                  lane, false);
-                    else
+                    } else if constexpr (SWIN) {
+                        // the speculative copy is stale: copy the window again (every
+                        // thread of the team finished reading it before the barrier above)
+                        stage_issue(e_cur);
+                        stage_wait(sb);
+                        lik_partial_staged<RES>(wmu, wcum, wcum2, BW, wdx, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw,
+                                                lt, NT, delta, red2 + twarp * 4, lane);
+                    } else {
                         lik_partial<T, RES, CUM, FINE>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
                                                  delta, muv, red2 + twarp * 4, lane, cq, cq2, false);
+                    }
                 }
                 __syncthreads();
+                if (SWIN && s_abort) {
+                    stage_drain();
+                    return;
+                }
                 if (active) decide();
             }
+            // the first round's successor, now that the neighbour wait is over
+            if (SANY && r == 0 && rounds > 1) stage_issue(e_cur + 1);
             if (active && nonfin && lt == 0) report_nonfinite(a.err, ch.chain, m, t, (double)dL, (double)dP);
             if (active) {
                 if (accept) {
@@ -753,9 +903,11 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                             int aa, bb, kw;
                             if (win_cell<FINE>(im, i, j, k, aa, bb, kw)) {
                                 // same value the proposal was scored with: still in registers when
-                                // the window took one batch, else reloaded (unchanged since)
+                                // the window took one batch (or in the staged copy), else reloaded
+                                // (unchanged since)
                                 const size_t idx = (size_t)aa * im.mu_pitch + bb;
-                                const T old = one_batch ? muv[jj] : __ldcg(mu_g + idx);
+                                const int widx = (k / L) * BW + wdx + (k - (k / L) * L);
+                                const T old = SWIN ? (T)wmu[widx] : one_batch ? muv[jj] : __ldcg(mu_g + idx);
                                 const T xk = mul_rn(delta, Ks[kw]);
                                 const T nmu = add_rn(old, xk);
                                 __stcg(mu_g + idx, nmu);
@@ -763,7 +915,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                                     const float d = (float)xk * Prec<float>::rcp((float)old);
                                     Cum6 nq;
                                     if (fabsf(d) <= kCumShift) {
-                                        nq = cgf_shift(__ldcg(cum_g + idx), __ldcg(cum2_g + idx), log1p_small(d));
+                                        if constexpr (SWIN) nq = cgf_shift(wcum[widx], wcum2[widx], log1p_small(d));
+                                        else nq = cgf_shift(__ldcg(cum_g + idx), __ldcg(cum2_g + idx), log1p_small(d));
                                     } else {
                                         const Dat4<T> dv = RES ? dat_s[(aa - a_lo) * rw + (bb - b_lo)] : dat_g[(size_t)aa * W + bb];
                                         nq = photon_cumulants_call((float)nmu, (float)dv.c, (float)dv.is2,
@@ -778,8 +931,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     for (int e = lt; e < sh.nhalf; e += NT) {
                         T wr, wi;
                         twiddle(tws, sh, ekl[sh.ent_off + e], u, v, wr, wi);
-                        spec_p[2 * e] = fma(delta, wr, spec_p[2 * e]);
-                        spec_p[2 * e + 1] = fma(delta, wi, spec_p[2 * e + 1]);
+                        spec_p[2 * e] = fma(delta, wr, spec_rd[2 * e]);
+                        spec_p[2 * e + 1] = fma(delta, wi, spec_rd[2 * e + 1]);
                     }
                     if (lt == 0) {
                         if (RES) rho_s[(size_t)q * S2 + u * S + v] = r_new;
@@ -848,7 +1001,12 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                 s_chg = 0;
             }
         }
+        // the next class step's first round: its windows overlap this step's,
+        // so its copy is issued after this step's writes (ordered by the
+        // barriers above) and checked against the neighbours after their wait
+        if (SANY) stage_issue((cs + 1) * rounds);
     }
+    if (SANY) stage_drain();
     // ---- epilogue: resident spectra back to global memory
     if (RES) {
         for (int q = 0; q < npt; ++q) {
@@ -863,11 +1021,15 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
 // The sweep kernel's form: tile state resident in shared memory or not,
 // augmented sampler or not, object lattice finer than the camera or not.
 template <typename T>
-const void* sweep_fn(bool res, bool aug, bool fine, bool solo)
+const void* sweep_fn(bool res, bool aug, bool fine, bool solo, int stg)
 {
-    if constexpr (std::is_same<T, float>::value)
+    if constexpr (std::is_same<T, float>::value) {
         if (solo && res && !fine)
             return aug ? (const void*)k_sweep<T, true, true, false, true> : (const void*)k_sweep<T, true, false, false, true>;
+        if (stg == 1 && !aug && !fine && !solo)
+            return res ? (const void*)k_sweep<T, true, false, false, false, 1>
+                       : (const void*)k_sweep<T, false, false, false, false, 1>;
+    }
     if (fine) {
         if (aug) return res ? (const void*)k_sweep<T, true, true, true> : (const void*)k_sweep<T, false, true, true>;
         return res ? (const void*)k_sweep<T, true, false, true> : (const void*)k_sweep<T, false, false, true>;
@@ -879,15 +1041,15 @@ const void* sweep_fn(bool res, bool aug, bool fine, bool solo)
 // Raise a kernel form's dynamic shared-memory limit to at least smem (the
 // limit only grows, so launches with smaller plans stay valid).
 template <typename T>
-cudaError_t ensure_smem_limit(bool res, bool aug, bool fine, bool solo, size_t smem)
+cudaError_t ensure_smem_limit(bool res, bool aug, bool fine, bool solo, int stg, size_t smem)
 {
-    static std::atomic<size_t> limit[16];
+    static std::atomic<size_t> limit[64];
     static std::mutex mu;
-    const int form = (res ? 1 : 0) | (aug ? 2 : 0) | (fine ? 4 : 0) | (solo ? 8 : 0);
+    const int form = (res ? 1 : 0) | (aug ? 2 : 0) | (fine ? 4 : 0) | (solo ? 8 : 0) | (stg << 4);
     if (limit[form].load() >= smem) return cudaSuccess;
     std::lock_guard<std::mutex> lock(mu);
     if (limit[form].load() >= smem) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(sweep_fn<T>(res, aug, fine, solo), cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(sweep_fn<T>(res, aug, fine, solo, stg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e == cudaSuccess) limit[form].store(smem);
     return e;
@@ -901,8 +1063,8 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
 {
     SweepArgs args = a;
     void* kargs[] = {&args};
-    const void* fn = sweep_fn<T>(a.resident, a.aug, a.fine, a.solo);
-    cudaError_t e = ensure_smem_limit<T>(a.resident, a.aug, a.fine, a.solo, smem);
+    const void* fn = sweep_fn<T>(a.resident, a.aug, a.fine, a.solo, a.stage);
+    cudaError_t e = ensure_smem_limit<T>(a.resident, a.aug, a.fine, a.solo, a.stage, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -918,19 +1080,22 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
 }
 
 // Blocks of the sweep kernel resident per SM for this block size and shared
-// memory (the smaller of its resident and streamed forms, so either fits).
+// memory: the smallest over its resident and streamed forms (and the one-team
+// form) so that either fits, or over the staged forms of a staging plan.
 template <typename T>
-int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine)
+int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine, int stg)
 {
     int best = 1 << 30;
     for (int form = 0; form < 4; ++form) {   // resident or not, x one-team form or not
-        const bool res = (form & 1) != 0, solo = (form & 2) != 0;
+        const bool res = (form & 1) != 0, solo = (form & 2) != 0 && stg == 0;
+        const int st = stg;
+        if (st != 0 && (solo || (form & 2) != 0)) continue;
         int n = 0;
-        if (ensure_smem_limit<T>(res, aug, fine, solo, smem) != cudaSuccess) {
+        if (ensure_smem_limit<T>(res, aug, fine, solo, st, smem) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_fn<T>(res, aug, fine, solo), threads, smem) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_fn<T>(res, aug, fine, solo, st), threads, smem) !=
             cudaSuccess)
             return 0;
         best = n < best ? n : best;
@@ -940,8 +1105,8 @@ int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine)
 
 template cudaError_t launch_sweep<float>(const SweepArgs&, int, int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs&, int, int, size_t, cudaStream_t);
-template int sweep_blocks_per_sm<float>(int, size_t, bool, bool);
-template int sweep_blocks_per_sm<double>(int, size_t, bool, bool);
+template int sweep_blocks_per_sm<float>(int, size_t, bool, bool, int);
+template int sweep_blocks_per_sm<double>(int, size_t, bool, bool, int);
 
 // ---------------------------------------------------------------- delta --
 // The same per-update arithmetic for one hypothetical proposal (testing):

@@ -15,6 +15,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "bdecon.h"
 #include "bd_internal.h"
 
@@ -48,6 +51,7 @@ struct ProbHost {
     size_t o_K64, o_K32, o_dat64, o_dat32, o_ekl, o_wa64, o_m64, o_wa32, o_m32, o_tw64, o_tw32, o_poff;
     size_t o_sum, o_sq, o_scr, o_samp, o_adapt;
     int samp_first = 0;         // first valid kept-object slot (after a resume)
+    bool stage_ok = false;      // its chains carry TMA tensor maps for window staging
     size_t scr_doubles;
     int chain0;
 };
@@ -66,11 +70,15 @@ struct Group {
     bool aug = false;                  // photon-count augmented problems (their own kernel form)
     bool fine = false;                 // object lattices finer than the camera (their own kernel form)
     bool solo = false;                 // every block: one patch, one team (a kernel form of its own)
+    int stage = 0;                     // window staging by the TMA engine (a kernel form): 1 on, 0 off
+    bool no_stage = true;              // window staging not allowed in this group's plan
+    bool user_stage = false;           // no_stage set by the autotuner, not by the handle's setting
     int chain_off = 0, n_chains = 0;   // slice of the group-ordered chain table
 };
 
 struct ChainHost {
     size_t o_rho, o_mu, o_spec, o_cum, o_cum2, o_tpart, o_acc, o_log, o_prog, o_trace, o_tdev, o_steps, o_phi;
+    size_t o_tmap = 0;
 };
 
 }  // namespace
@@ -85,6 +93,7 @@ struct bdecon_handle {
     int64_t sweeps = 0;
     std::vector<Group> groups;
     bool one_launch = false;            // all problems in one launch instead of one per (L, S, team)
+    int staging = 0;                    // window staging by the TMA engine in eligible groups (1) or not (0)
     std::vector<int> prob_group;        // problem -> group
     std::vector<Chain> gch;             // host copy of the group-ordered chain table
     size_t o_gchains = 0;
@@ -258,15 +267,17 @@ void describe(ProbHost& ph)
         for (int pj = 0; pj < ph.npj; ++pj) {
             const int s = (((pi + 1) * ph.S > ph.Ho) ? 2 : 0) | (((pj + 1) * ph.S > ph.Wo) ? 1 : 0);
             ph.patch_off[pi * ph.npj + pj] = off;
-            off += ph.shape[s].nhalf;
+            // even offsets: every patch's half spectrum starts 16-byte aligned in
+            // float (the staged plans copy it with one bulk copy)
+            off += (ph.shape[s].nhalf + 1) & ~1;
         }
     ph.spec_len = off;
 }
 
-int occupancy(int prec, int threads, size_t smem, bool aug, bool fine)
+int occupancy(int prec, int threads, size_t smem, bool aug, bool fine, int stg)
 {
-    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug, fine)
-                               : sweep_blocks_per_sm<double>(threads, smem, aug, fine);
+    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug, fine, stg)
+                               : sweep_blocks_per_sm<double>(threads, smem, aug, fine, stg);
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
@@ -286,27 +297,35 @@ int item_blocks(const PlanItem& it)
     return (int)it.chains.size() * ((it.ph->npi + it.tpi - 1) / it.tpi) * ((it.ph->npj + it.tpj - 1) / it.tpj);
 }
 
-size_t items_smem(const std::vector<PlanItem*>& items, int resident, int ts, int threads)
+size_t items_smem(const std::vector<PlanItem*>& items, int resident, int ts, int threads, int stage)
 {
     size_t mx = 0;
     for (const PlanItem* it : items) {
         const ProbHost& ph = *it->ph;
         const int teams = std::max(1, threads / it->team);   // update teams per block
         const SmemPlan sp = smem_plan(ph.L, ph.f, ph.S, ph.n_tw, (int)ph.ent_kl.size(), ph.max_nhalf, it->tpi,
-                                      it->tpj, resident, ts, teams);
+                                      it->tpj, resident, ts, teams, stage);
         mx = std::max(mx, sp.total);
     }
     return mx;
 }
 
-// Grow the tile of the problem with the most blocks; false if none can grow.
+// Grow the tile of the problem whose tiles are smallest (ties: the one with
+// the most blocks); false if none can grow.  A launch lasts as long as its
+// slowest chain, and a block takes one round per patch of its tile at every
+// class step, so the launch is fastest when every problem's tiles hold about
+// the same number of patches; growing the problem with the most blocks
+// instead gives the largest frames of a batch the largest tiles.
 bool grow_items(std::vector<PlanItem*>& items)
 {
     PlanItem* worst = nullptr;
-    int wb = -1;
+    int wa = 1 << 30, wb = -1;
     for (PlanItem* it : items) {
+        if (it->user || (it->tpi >= it->ph->npi && it->tpj >= it->ph->npj)) continue;
+        const int area = std::min(it->tpi, it->ph->npi) * std::min(it->tpj, it->ph->npj);
         const int b = item_blocks(*it);
-        if (!it->user && !(it->tpi >= it->ph->npi && it->tpj >= it->ph->npj) && b > wb) {
+        if (area < wa || (area == wa && b > wb)) {
+            wa = area;
             wb = b;
             worst = it;
         }
@@ -328,26 +347,63 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
     g.threads = g.user_warps ? std::max(32 * g.warps, team) : team;
     g.warps = g.threads / 32;
     const int ts = precision == BDECON_FP32 ? 4 : 8;
+    // window staging: float marginal camera-grid problems whose chains carry
+    // tensor maps, when the handle (or the autotuner) asks for it; a plan in
+    // which every block updates one patch with one team keeps the one-team
+    // form instead (its windows are read once per step from L2 by many blocks
+    // at once, and it needs no buffers)
+    bool stage_ok = precision == BDECON_FP32 && !g.aug && !g.fine && !g.no_stage;
+    for (const PlanItem* it : items) stage_ok = stage_ok && it->ph->stage_ok;
     bool done = false;
-    for (int resident = g.streamed ? 0 : 1; resident >= 0 && !done; --resident) {
-        for (PlanItem* it : items)
-            if (!it->user) it->tpi = it->tpj = 1;
-        for (;;) {
-            const size_t smem = items_smem(items, resident, ts, g.threads);
-            int tot = 0;
-            for (const PlanItem* it : items) tot += item_blocks(*it);
-            if (smem <= kMaxSmem) {
-                const int bps = occupancy(precision, g.threads, smem, g.aug, g.fine);
+    for (int attempt = stage_ok ? 0 : 1; attempt < 2 && !done; ++attempt) {
+        for (int resident = g.streamed ? 0 : 1; resident >= 0 && !done; --resident) {
+            const int stage = attempt == 0 ? 1 : 0;
+            for (PlanItem* it : items)
+                if (!it->user) it->tpi = it->tpj = 1;
+            for (;;) {
+                const size_t smem = items_smem(items, resident, ts, g.threads, stage);
+                int tot = 0;
+                for (const PlanItem* it : items) tot += item_blocks(*it);
+                if (smem <= kMaxSmem) {
+                    const int bps = occupancy(precision, g.threads, smem, g.aug, g.fine, stage);
+                    if (bps > 0 && tot <= bps * sms) {
+                        g.smem = smem;
+                        g.resident = resident;
+                        g.stage = stage;
+                        done = true;
+                        break;
+                    }
+                } else if (resident) {
+                    break;   // tiles only grow: resident state will not fit
+                }
+                if (!grow_items(items)) break;
+            }
+        }
+        if (done && attempt == 0) {
+            // a one-patch one-team plan without staging runs the one-team form
+            bool solo_ok = true;
+            std::vector<std::pair<int, int>> keep;
+            for (PlanItem* it : items) keep.push_back({it->tpi, it->tpj});
+            for (PlanItem* it : items) {
+                if (!it->user) it->tpi = it->tpj = 1;
+                solo_ok = solo_ok && it->tpi == 1 && it->tpj == 1 && g.threads == it->team;
+            }
+            if (solo_ok) {
+                const size_t smem = items_smem(items, 1, ts, g.threads, 0);
+                int tot = 0;
+                for (const PlanItem* it : items) tot += item_blocks(*it);
+                const int bps = smem <= kMaxSmem ? occupancy(precision, g.threads, smem, g.aug, g.fine, 0) : 0;
                 if (bps > 0 && tot <= bps * sms) {
                     g.smem = smem;
-                    g.resident = resident;
-                    done = true;
+                    g.resident = 1;
+                    g.stage = 0;
                     break;
                 }
-            } else if (resident) {
-                break;   // tiles only grow: resident state will not fit
             }
-            if (!grow_items(items)) break;
+            for (size_t k = 0; k < items.size(); ++k) {
+                items[k]->tpi = keep[k].first;
+                items[k]->tpj = keep[k].second;
+            }
         }
     }
     if (!done) {
@@ -358,7 +414,7 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
         err = buf;
         return false;
     }
-    g.solo = true;
+    g.solo = g.stage == 0;
     for (const PlanItem* it : items) g.solo = g.solo && it->tpi == 1 && it->tpj == 1 && g.threads == it->team;
     int base = 0;
     for (PlanItem* it : items) {
@@ -385,6 +441,7 @@ bdecon_status make_plan(bdecon_handle* h)
 {
     drop_graphs(h);   // captured launches carry the old grid and tables
     for (auto& g : h->groups) {
+        if (!g.user_stage) g.no_stage = h->staging == 0;
         std::vector<PlanItem> items(g.probs.size());
         std::vector<PlanItem*> ptrs;
         for (size_t k = 0; k < g.probs.size(); ++k) {
@@ -451,6 +508,47 @@ void form_groups(bdecon_handle* h)
     }
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// The window-staging tensor maps of one float chain: mu (H x W floats, row
+// pitch mu_pitch), the cumulants c1..c4 (H x 4W floats) and c5, c6 (H x 2W
+// floats); boxes of stage_w(L) pixels by L rows, zeros outside the frame.
+bool encode_stage_maps(const ProbHost& ph, const Chain& ch, CUtensorMap out[3])
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint32_t BW = (cuuint32_t)stage_w(ph.L), L = (cuuint32_t)ph.L;
+    const cuuint32_t es[2] = {1, 1};
+    void* base[3] = {ch.mu, ch.cum, ch.cum2};
+    const int per[3] = {1, 4, 2};   // floats per pixel
+    for (int k = 0; k < 3; ++k) {
+        const cuuint64_t dims[2] = {(cuuint64_t)per[k] * ph.W, (cuuint64_t)ph.H};
+        const cuuint64_t strides[1] = {(cuuint64_t)per[k] * 4 * ph.pitch};
+        const cuuint32_t box[2] = {per[k] * BW, L};
+        if (enc(&out[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base[k], dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
 size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainHost>& chh, int prec, int max_sweeps)
 {
     Alloc A;
@@ -503,6 +601,8 @@ size_t layout(bdecon_handle* h, std::vector<ProbHost>& probs, std::vector<ChainH
             x.o_trace = A.take(8 * ((size_t)max_sweeps + 1));
             x.o_tdev = A.take(4);
             x.o_steps = adapt ? A.take(ts * nobj) : 0;
+            // window staging: three 128-byte TMA tensor maps (64-byte aligned)
+            x.o_tmap = prec == BDECON_FP32 && !aug && ph.f == 1 && ph.L <= kStageMaxL ? A.take(3 * sizeof(CUtensorMap)) : 0;
             chh.push_back(x);
         }
     }
@@ -638,7 +738,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         im.patch_off = (const int64_t*)(A + ph.o_poff);
         im.spec_len = ph.spec_len;
         im.n_ent = (int)ph.ent_kl.size();
-        im.team = problem_team(ph.Lc, ph.p.n_chains, ph.n_patches, ph.p.team_warps);
+        im.team = problem_team(ph.Lc, ph.p.n_chains, ph.n_patches, ph.p.team_warps, h->precision == BDECON_FP32);
         im.n_tw = ph.n_tw;
         im.max_nhalf = ph.max_nhalf;
         im.sample_every = ph.p.sample_every > 0 ? ph.p.sample_every : 1;
@@ -670,7 +770,24 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
                                    : nullptr;
             ch.steps = x.o_steps ? A + x.o_steps : nullptr;
             ch.phi = x.o_phi ? A + x.o_phi : nullptr;
+            ch.tmap = x.o_tmap ? A + x.o_tmap : nullptr;
         }
+    }
+    // window-staging tensor maps (a problem without them runs unstaged plans)
+    for (int k = 0; k < n; ++k) {
+        ProbHost& ph = h->probs[k];
+        ph.stage_ok = true;
+        for (int c = 0; c < ph.p.n_chains && ph.stage_ok; ++c) {
+            Chain& ch = h->chains[ph.chain0 + c];
+            CUtensorMap maps[3];
+            if (!ch.tmap || !encode_stage_maps(ph, ch, maps) ||
+                cudaMemcpyAsync((void*)ch.tmap, maps, sizeof maps, cudaMemcpyHostToDevice, h->st) != cudaSuccess) {
+                cudaGetLastError();
+                ph.stage_ok = false;
+            }
+        }
+        if (!ph.stage_ok)
+            for (int c = 0; c < ph.p.n_chains; ++c) h->chains[ph.chain0 + c].tmap = nullptr;
     }
     if (cudaMemcpyAsync(h->d_imgs, h->imgs.data(), sizeof(Image) * n, cudaMemcpyHostToDevice, h->st) != cudaSuccess)
         return bail(fail(h, BDECON_ERR_CUDA, "descriptor upload"));
@@ -852,6 +969,7 @@ bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle
         a.aug = g.aug ? 1 : 0;
         a.fine = g.fine ? 1 : 0;
         a.solo = g.solo ? 1 : 0;
+        a.stage = g.stage;
         cudaError_t e = eh->precision == BDECON_FP32 ? launch_sweep<float>(a, g.grid, g.threads, g.smem, st)
                                                      : launch_sweep<double>(a, g.grid, g.threads, g.smem, st);
         if (e != cudaSuccess)
@@ -1428,6 +1546,34 @@ bdecon_status bdecon_set_grouping(bdecon_handle* h, int32_t one_launch)
     return s;
 }
 
+bdecon_status bdecon_set_staging(bdecon_handle* h, int32_t enable)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    bdecon_status s = check_device(h);
+    if (s != BDECON_OK) return s;
+    const int old = h->staging;
+    const std::vector<Group> old_groups = h->groups;
+    h->staging = enable != 0 ? 1 : 0;
+    for (auto& g : h->groups) g.user_stage = false;
+    s = make_plan(h);
+    if (s != BDECON_OK) {
+        const std::string m = h->err;
+        h->staging = old;
+        h->groups = old_groups;
+        make_plan(h);
+        h->err = m;
+    }
+    return s;
+}
+
+bdecon_status bdecon_get_staging(bdecon_handle* h, int32_t p, int32_t* staged)
+{
+    if (!h || !staged) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    if (p < 0 || p >= (int)h->probs.size()) return fail(h, BDECON_ERR_INVALID, "problem index %d", p);
+    *staged = h->groups[h->prob_group[p]].stage;
+    return BDECON_OK;
+}
+
 namespace {
 
 // One autotuner trial: a segment of len sweeps in the current plan, timed
@@ -1455,6 +1601,7 @@ bdecon_status tune_trial(bdecon_handle* h, int len, std::vector<double>& ms)
 struct TuneChoice {
     int warps = 0;          // 0: the team's own
     bool streamed = false;
+    bool staged = false;
     double ms = 1e300;
 };
 
@@ -1494,24 +1641,31 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
     h->one_launch = false;
     form_groups(h);
     std::vector<TuneChoice> best(h->groups.size());
-    for (int streamed = 0; streamed <= 1 && s == BDECON_OK; ++streamed)
-        for (int mi = 0; mi < 3 && s == BDECON_OK; ++mi) {
-            bool any = false;
-            for (auto& g : h->groups) {
-                const int tw = g.team / 32, w = std::min(8, tw * kMult[mi]);
-                any = any || (mi == 0 || w != std::min(8, tw * kMult[mi - 1]));
-                g.warps = w;
-                g.user_warps = true;
-                g.streamed = streamed != 0;
+    bool any_stage = false;   // window staging is a candidate only where some problem allows it
+    for (const auto& ph : h->probs) any_stage = any_stage || ph.stage_ok;
+    // (staged shapes are tried with the team's own warps only: their buffers
+    // already limit the blocks per SM)
+    for (int st = 0; st <= (any_stage ? 1 : 0) && s == BDECON_OK; ++st)
+        for (int streamed = 0; streamed <= 1 && s == BDECON_OK; ++streamed)
+            for (int mi = 0; mi < (st ? 1 : 3) && s == BDECON_OK; ++mi) {
+                bool any = false;
+                for (auto& g : h->groups) {
+                    const int tw = g.team / 32, w = std::min(8, tw * kMult[mi]);
+                    any = any || (mi == 0 || w != std::min(8, tw * kMult[mi - 1]));
+                    g.warps = w;
+                    g.user_warps = true;
+                    g.streamed = streamed != 0;
+                    g.no_stage = st == 0;
+                    g.user_stage = true;
+                }
+                if (!any) continue;
+                if (make_plan(h) != BDECON_OK) continue;   // no co-resident plan of this shape
+                std::vector<double> ms;
+                s = tune_trial(h, len, ms);
+                if (s == BDECON_OK) s = restore();
+                for (size_t g = 0; g < ms.size() && s == BDECON_OK; ++g)
+                    if (ms[g] < best[g].ms) best[g] = {h->groups[g].warps, streamed != 0, h->groups[g].stage == 1, ms[g]};
             }
-            if (!any) continue;
-            if (make_plan(h) != BDECON_OK) continue;   // no co-resident plan of this shape
-            std::vector<double> ms;
-            s = tune_trial(h, len, ms);
-            if (s == BDECON_OK) s = restore();
-            for (size_t g = 0; g < ms.size() && s == BDECON_OK; ++g)
-                if (ms[g] < best[g].ms) best[g] = {h->groups[g].warps, streamed != 0, ms[g]};
-        }
     double t_groups = 0;
     for (const auto& b : best) t_groups += b.ms;
     // (b) one launch over every problem
@@ -1521,20 +1675,23 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
         form_groups(h);
         Group& g = h->groups[0];
         bool behind = false;   // the first shapes are far slower than per-group launches: stop trying
-        for (int streamed = 0; streamed <= 1 && s == BDECON_OK && !behind; ++streamed)
-            for (int mi = 0; mi < 3 && s == BDECON_OK && !behind; ++mi) {
-                const int w = std::min(8, (g.team / 32) * kMult[mi]);
-                if (mi > 0 && w == std::min(8, (g.team / 32) * kMult[mi - 1])) continue;
-                g.warps = w;
-                g.user_warps = true;
-                g.streamed = streamed != 0;
-                if (make_plan(h) != BDECON_OK) continue;
-                std::vector<double> ms;
-                s = tune_trial(h, len, ms);
-                if (s == BDECON_OK) s = restore();
-                if (s == BDECON_OK && ms[0] < one.ms) one = {w, streamed != 0, ms[0]};
-                behind = s == BDECON_OK && one.ms > 1.5 * t_groups;
-            }
+        for (int st = 0; st <= (any_stage ? 1 : 0) && s == BDECON_OK && !behind; ++st)
+            for (int streamed = 0; streamed <= 1 && s == BDECON_OK && !behind; ++streamed)
+                for (int mi = 0; mi < (st ? 1 : 3) && s == BDECON_OK && !behind; ++mi) {
+                    const int w = std::min(8, (g.team / 32) * kMult[mi]);
+                    if (mi > 0 && w == std::min(8, (g.team / 32) * kMult[mi - 1])) continue;
+                    g.warps = w;
+                    g.user_warps = true;
+                    g.streamed = streamed != 0;
+                    g.no_stage = st == 0;
+                    g.user_stage = true;
+                    if (make_plan(h) != BDECON_OK) continue;
+                    std::vector<double> ms;
+                    s = tune_trial(h, len, ms);
+                    if (s == BDECON_OK) s = restore();
+                    if (s == BDECON_OK && ms[0] < one.ms) one = {w, streamed != 0, g.stage == 1, ms[0]};
+                    behind = s == BDECON_OK && one.ms > 1.5 * t_groups;
+                }
     }
     // apply the fastest
     if (s == BDECON_OK) {
@@ -1544,11 +1701,15 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
             h->groups[0].warps = one.warps;
             h->groups[0].user_warps = true;
             h->groups[0].streamed = one.streamed;
+            h->groups[0].no_stage = !one.staged;
+            h->groups[0].user_stage = true;
         } else {
             for (size_t g = 0; g < h->groups.size(); ++g) {
                 h->groups[g].warps = best[g].warps;
                 h->groups[g].user_warps = true;
                 h->groups[g].streamed = best[g].streamed;
+                h->groups[g].no_stage = !best[g].staged;
+                h->groups[g].user_stage = true;
             }
         }
         s = make_plan(h);
