@@ -1,19 +1,31 @@
 """Benchmark of the posterior-sampling sweep (pixel-updates/s).
 
-Workload: the 512x512 sCMOS widefield frame (PSF sigma ~1.2 px on 17x17,
-offset/variance maps, gain 2.1, 1 chain), float sweep form.  One step = 50
-sweeps of every chain = one refresh period: the sweep kernel (propose,
-window likelihood change, patch prior change, accept/write, running mean)
-followed by the double-precision refresh of mu, spectra and log posterior
-and the trace assembly.  Inputs are resident in HBM; L2 is flushed (a 256 MB
-write) between timed steps because the working set (~10 MB) fits in L2.
+Headline (value): the float form, batched -- 64 frames of uneven sizes
+(sides 128..1024, Gaussian PSF sigma 1..4 px on 2 ceil(3 sigma)+1 support,
+peak 3..200 photons) x 4 chains each in one handle, launch shapes picked by
+the library's autotuner, every sweep call replayed as one CUDA graph.  One
+step = 10 sweeps of every chain followed by the double refresh (expected
+image, spectra, cumulant cache, log posterior) and the trace: every row of
+the hot path (propose, window likelihood change, patch prior change,
+accept/write, class schedule, running mean, refresh).  The chains' state
+(~5 GB) is far larger than L2, so no flush is needed between steps.
 
-value     pixel-updates/s of the float form (object pixels x chains x sweeps / s)
-e2e       same metric through the C ABI from host buffers: create (H2D of frame
-          and maps, set-up, initial refresh), 50 sweeps, posterior mean (D2H)
-fp64      the plain double sampler on the same frame (extra key)
-roofline  sweep kernel, plain-ALU bound (see the design doc for the op count)
-cpu_baseline  the C oracle on a 128x128 crop of the same frame, 1 sweep per core
+e2e       the same metric through the C ABI from pinned host buffers: create
+          (H2D of the 64 frames, set-up, first refresh), one step of sweeps,
+          posterior means of every frame (D2H)
+roofline  the sweep kernel against the plain-ALU peak (SMs x 128 FP32 lanes x
+          2 x max SM clock), with the algorithmic work per update
+          L^2 (4 n + 10) + 12 S^2 (n the photon counts carrying >= 2^-26 of a
+          pixel's photon posterior); bw_roofline: 68 algorithmic bytes per
+          update against the measured HBM copy bandwidth
+legs      fp64_plain (the plain double sampler on frames of the same batch),
+          widefield_512 (512x512 sCMOS frame, L = 17, 1 chain, float and double),
+          widefield_64 (64x64 frame, L = 9, double, 200 sweeps),
+          lowsnr_2048 (2048x2048 low-SNR frame, L = 31, 4 chains, float and double),
+          serving (Poisson arrivals at 20 jobs/s, float and double arms)
+cpu_baseline  the C oracle timed on the host cores on a bounded sample of the
+          batch (crops of its frames, one chain per core); the same leg then
+          evaluates, with the oracle, the error of each GPU result
 
 --impl reference runs the oracle (the CPU restatement of the method) as the
 reference arm on the host cores, on a bounded sample of the same workload.
@@ -21,6 +33,7 @@ reference arm on the host cores, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import math
 import multiprocessing as mp
@@ -39,8 +52,10 @@ if ROOT not in sys.path:
 from paper_2411_00991_gb300 import synth  # noqa: E402
 
 METRIC = "pixel-updates/s, FP32 batched vs FP64 plain on one GB300; % of BW roofline"
-SWEEPS_PER_STEP = 50
-CROP = 128
+SWEEPS_PER_STEP = 10
+N_IMAGES = 64
+CROP = 96
+FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 rate (no measured figure on this machine)
 
 
 def _peaks():
@@ -48,7 +63,7 @@ def _peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
         return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070.0)),
-                    source="measured")
+                    source="measured (MEASURED_PEAKS.json)")
     except Exception:
         return dict(hbm_gbs=6800.0, sm_max_mhz=2070.0, source="fallback")
 
@@ -100,141 +115,325 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
+# ------------------------------------------------------------ workloads --
+def batch_problems(rank=0, n_images=N_IMAGES):
+    """The batched workload (64 uneven frames x 4 chains); each rank of a
+    multi-GPU run takes its own frames (seeds offset by rank)."""
+    probs = synth.batch_uneven(n_images, seed0=3000 + 1000 * rank)
+    for q in probs:
+        q.burn_in = 0                     # every sweep enters the running mean
+        q.refresh_every = SWEEPS_PER_STEP
+        q.truth = None
+    return probs
+
+
+def obj_updates(probs):
+    return sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * q.n_chains for q in probs)
+
+
+# ------------------------------------------------------------ op counting --
+def photon_terms(prob, mu, max_pixels=40000):
+    """Mean number of photon counts carrying >= 2^-26 of a camera pixel's
+    photon posterior p(phi | w, mu) at the current expected image (a seeded
+    sample of at most max_pixels pixels)."""
+    from scipy.special import gammaln
+    g, o, v = prob.maps()
+    c = ((prob.image.astype(np.float64) - o) / g).ravel()
+    s2 = (v / g ** 2).ravel()
+    mu = np.maximum(np.asarray(mu, dtype=np.float64).ravel(), 1e-12)
+    if c.size > max_pixels:
+        idx = np.random.default_rng(0).choice(c.size, max_pixels, replace=False)
+        c, s2, mu = c[idx], s2[idx], mu[idx]
+    phi = np.arange(0, int(max(c.max(), mu.max()) + 60))[:, None]
+    lt = -(c[None, :] - phi) ** 2 / (2 * s2[None, :]) + phi * np.log(mu[None, :]) - gammaln(phi + 1)
+    lt -= lt.max(axis=0, keepdims=True)
+    w = np.exp(lt)
+    w /= w.sum(axis=0, keepdims=True)
+    return float((w >= 2.0 ** -26).sum(axis=0).mean())
+
+
+def flops_per_update(L, S, nterms):
+    """Algorithmic FP32 operations of one pixel update: L^2 window pixels at
+    4 per photon-count term + 10, and 12 per patch spectrum entry (S^2)."""
+    return L * L * (4.0 * nterms + 10.0) + 12.0 * S * S
+
+
+BYTES_PER_UPDATE = 68.0      # rho, mu, cumulant cache r/w; w, o, var; spectrum r/w; double mean r/w
+
+
+def alu_peak_tflops(dev, sm_mhz):
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12, sms
+
+
+def roofline(flops, kernel_ms, launches, updates, dev, peaks, kernel, fp64=False):
+    """Roofline of a sweep kernel from its algorithmic work and its measured
+    device time (summed over `launches` launches)."""
+    sec = kernel_ms / 1e3
+    if fp64:
+        peak, src = FP64_PEAK_TFLOPS, "GB300 nominal FP64 rate (no measured FP64 figure)"
+        sms = None
+    else:
+        peak, sms = alu_peak_tflops(dev, peaks["sm_max_mhz"])
+        src = f"{sms} SMs (device query) x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz max SM clock"
+    ach = flops / sec / 1e12
+    gbs = BYTES_PER_UPDATE * (2 if fp64 else 1) * updates / sec / 1e9
+    return ({"bound": "alu", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+             "frac": ach / peak, "traffic": None, "flops_per_launch": flops / max(launches, 1),
+             "launch_ms": kernel_ms / max(launches, 1), "launches": launches,
+             "flops_formula": "updates x [L^2 (4 n + 10) + 12 S^2]", "peak_source": src},
+            {"achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+             "bytes_per_update": BYTES_PER_UPDATE * (2 if fp64 else 1), "peak_source": peaks["source"]})
+
+
 # ----------------------------------------------------------- CPU baseline --
-def crop_problem(prob, side=CROP, y0=192, x0=192):
-    """A side x side region of the frame with its maps: a bounded sample of
-    the same workload (same PSF, camera model, structure density)."""
-    import copy
+def crop_problem(prob, side=CROP, y0=None, x0=None):
+    """A side x side region of a frame with its maps: a bounded sample of the
+    same workload (same PSF, camera model, structure density)."""
     q = copy.copy(prob)
+    y0 = (prob.H - side) // 2 if y0 is None else y0
+    x0 = (prob.W - side) // 2 if x0 is None else x0
     sl = (slice(y0, y0 + side), slice(x0, x0 + side))
     q.image = np.ascontiguousarray(prob.image[sl])
-    q.offset = prob.offset if np.isscalar(prob.offset) else np.ascontiguousarray(prob.offset[sl])
-    q.var = prob.var if np.isscalar(prob.var) else np.ascontiguousarray(prob.var[sl])
-    q.gain = prob.gain if np.isscalar(prob.gain) else np.ascontiguousarray(prob.gain[sl])
+    for k in ("offset", "var", "gain"):
+        v = getattr(prob, k)
+        setattr(q, k, v if np.isscalar(v) else np.ascontiguousarray(v[sl]))
     q.truth = None
     q.name = prob.name + f"_crop{side}"
     return q
 
 
-def _oracle_job(args):
-    seed, sweeps = args
+def _oracle_job(k):
     from oracle import oracle as O
-    prob = crop_problem(synth.widefield_512())
-    prob.seed = seed
+    prob = crop_problem(synth.batch_frame(k % N_IMAGES))
+    prob.burn_in, prob.refresh_every = 0, SWEEPS_PER_STEP
     orc = O.Oracle(prob)
     t = time.perf_counter()
-    orc.run(sweeps)
+    orc.run(1)
     dt = time.perf_counter() - t
     Ho, Wo = prob.object_shape()
-    return Ho * Wo * sweeps, dt
+    return Ho * Wo, dt
 
 
-def cpu_baseline(sweeps=1, cores=None):
+def cpu_baseline(cores=None):
     """The oracle as it stands, one independent chain per host core (spawned
-    processes), on the 128x128 crop; returns updates/s over the wall time."""
+    processes), one sweep of a 96x96 crop of batch frame k on core k, all
+    cores at once; returns the updates of all cores over the longest core's
+    sweep time."""
     from oracle import oracle as O
     O.build()
     n = cores or min(os.cpu_count() or 1, 16)
-    ctx = mp.get_context("spawn")
-    t = time.perf_counter()
-    with ctx.Pool(n) as pool:
-        res = pool.map(_oracle_job, [(1000 + k, sweeps) for k in range(n)])
-    wall = time.perf_counter() - t
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_job, range(n))
     upd = sum(r[0] for r in res)
-    per_proc = float(np.mean([r[0] / r[1] for r in res]))
-    return dict(value=upd / wall, unit="pixel-updates/s", cores=n, kind="oracle",
-                sample=f"{CROP}x{CROP} crop of the 512x512 frame (L=17), {sweeps} sweep(s) per core, "
-                       f"one chain per core; wall {wall:.1f} s incl. process start",
-                per_core=per_proc)
+    slowest = max(r[1] for r in res)
+    return dict(value=upd / slowest, unit="pixel-updates/s", cores=n, kind="oracle",
+                sample=f"one sweep of a {CROP}x{CROP} crop of batch frame k on core k (k < {n}, PSF sides "
+                       f"{sorted({synth.batch_frame(k).L for k in range(n)})}), one chain per core, "
+                       f"longest core {slowest:.1f} s",
+                per_core=float(np.mean([r[0] / r[1] for r in res])))
 
 
-# ------------------------------------------------------------ op counting --
-def flops_per_update(prob, mu):
-    """Algorithmic float operations of one update (FMA = 2): for each window
-    pixel 6 per photon-count term (term, Gaussian factor, power and sum
-    recurrences) + 40 fixed (mode, logs, ratios), for each half-spectrum
-    entry of the patch 22.  The term count is the number of photon counts
-    carrying >= 2^-26 of the pixel's photon posterior at the current mu."""
-    g, o, v = prob.maps()
-    c = (prob.image.astype(np.float64) - o) / g
-    s2 = v / g ** 2
-    mu = np.maximum(mu, 1e-12)
-    phi = np.arange(0, int(max(c.max(), mu.max()) + 60))[:, None]
-    cf, s2f, muf = c.ravel()[None, :], s2.ravel()[None, :], mu.ravel()[None, :]
-    from scipy.special import gammaln
-    lt = -(cf - phi) ** 2 / (2 * s2f) + phi * np.log(muf) - gammaln(phi + 1)
-    lt -= lt.max(axis=0, keepdims=True)
-    w = np.exp(lt)
-    w /= w.sum(axis=0, keepdims=True)
-    nterms = float((w >= 2.0 ** -26).sum(axis=0).mean())
-    L = prob.L
-    nhalf = (prob.S * prob.S + 1) // 2
-    return L * L * (6 * nterms + 40) + nhalf * 22, nterms
+def _rel(a, b):
+    return abs(a - b) / abs(b)
 
 
-# ---------------------------------------------------------- batched form --
-def run_batched(stream, sweeps=2, warm=1, n_images=64):
-    """The batched float form: 64 uneven frames (sides 128..1024, PSF sigma
-    1..4 px, support 2 ceil(3 sigma)+1) x 4 chains in one handle.  Timed
-    first in the automatic plan (one cooperative launch per PSF side), then
-    after the library's autotuner picked the launch shapes, with every sweep
-    call replayed as one CUDA graph."""
-    import torch
-    from paper_2411_00991_gb300 import bdecon
-    probs = synth.batch_uneven(n_images)
-    for q in probs:
-        q.burn_in = 0
-        q.refresh_every = 50
-    upd = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * q.n_chains for q in probs)
-    s = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=2 * (warm + sweeps) + 8, stream=stream)
+def _eval_job(args):
+    prob, rho = args
+    from oracle import oracle as O
+    return O.Oracle(prob).log_posterior_fft(rho)
 
-    def timed():
-        s.sweep(warm)
-        s.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n0 = s.launch_count()
-        e0.record()
-        s.sweep(sweeps)
-        e1.record()
-        torch.cuda.synchronize()
-        s.sync()
-        return e0.elapsed_time(e1), s.launch_count() - n0
 
-    ms_auto, _ = timed()
-    t = time.perf_counter()
-    tune = s.autotune(trial_sweeps=1)
-    tune_s = time.perf_counter() - t
-    s.set_graph(True)
-    ms, launches = timed()
-    groups = len({json.dumps(s.get_plan(p)) for p in range(len(probs))})
-    out = dict(value=upd * sweeps / (ms / 1e3), unit="pixel-updates/s", images=len(probs),
-               chains=sum(q.n_chains for q in probs), updates_per_sweep=upd, sweeps=sweeps,
-               ms_per_sweep=ms / sweeps, gpu_launches=launches, cuda_graph=True,
-               autotune=dict(one_launch=tune["one_launch"], trial_ms_per_sweep=tune["ms_per_sweep"],
-                             seconds=tune_s),
-               distinct_plans=groups,
-               automatic_plan=dict(value=upd * sweeps / (ms_auto / 1e3), ms_per_sweep=ms_auto / sweeps))
-    s.close()
+def oracle_errors(checks, exact64):
+    """Error of the GPU results against the oracle: each trace value (the
+    float chains' double running sum) against the oracle's Eq. 9 of the
+    chain's own state; the double chain on the 64x64 frame against the
+    oracle's chain (accept decisions, object, trace)."""
+    from oracle import oracle as O
+    out = {}
+    with mp.get_context("spawn").Pool(min(len(checks), os.cpu_count() or 4, 16)) as pool:
+        refs = pool.map(_eval_job, [(c["prob"], c["rho"]) for c in checks])
+    for c, ref in zip(checks, refs):
+        out.setdefault(c["leg"], []).append({"what": c["what"], "trace": c["trace"], "oracle": ref,
+                                             "rel_err": _rel(c["trace"], ref)})
+    if exact64 is not None:
+        prob, g = exact64
+        ref = O.Oracle(prob).run(g["sweeps"], want_acc_log=True)
+        out["widefield_64"] = {"what": f"double chain vs the oracle's chain, {g['sweeps']} sweeps",
+                               "accept_mismatches": int((g["acc"] != ref["acc_log"]).sum()),
+                               "rho_max_rel_err": float(np.max(np.abs(g["rho"] - ref["rho"]) / ref["rho"])),
+                               "trace_max_rel_err": float(np.max(np.abs(g["trace"] - ref["trace"]) /
+                                                                 np.abs(ref["trace"])))}
     return out
 
 
-# --------------------------------------------------------------- serving --
-def run_serving(n_jobs=8, sweeps=500, rate=20.0, budget_gb=120):
+# -------------------------------------------------------------- helpers --
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def timed_sweeps(s, n, stream, torch):
+    e0, e1 = _events(torch)
+    e0.record(stream)
+    s.sweep(n)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s.sync()
+    return e0.elapsed_time(e1)
+
+
+def kernel_time(s, n):
+    """Device time of the sweep-kernel launches of n plain (non-graph) sweeps."""
+    s.set_timing(True)
+    s.sweep_kernel_time()
+    s.sweep(n)
+    s.sync()
+    ms, launches = s.sweep_kernel_time()
+    s.set_timing(False)
+    return ms, launches
+
+
+def _pinned_copy(prob, torch):
+    """The problem with its frame and maps in pinned host memory."""
+    q = copy.copy(prob)
+    for k in ("image", "offset", "var", "gain"):
+        v = getattr(prob, k)
+        if not np.isscalar(v):
+            t = torch.empty(np.asarray(v).shape, dtype=torch.float32, pin_memory=True)
+            a = t.numpy()
+            a[...] = v
+            setattr(q, k, a)
+    return q
+
+
+# ----------------------------------------------------------------- legs --
+def leg_fp64_batch(bd, stream, torch, dev, peaks, rank, n_images=8):
+    """The plain double sampler on the first n_images frames of the batch,
+    against the float form on the same frames (same sweeps)."""
+    probs = batch_problems(rank)[:n_images]
+    upd = obj_updates(probs)
+    out = {"workload": f"frames 0..{n_images - 1} of the batch ({[q.H for q in probs]} px sides, "
+                       f"L {[q.L for q in probs]}), 4 chains each, 1 sweep"}
+    for name, prec in (("fp64", bd.BDECON_FP64), ("fp32", bd.BDECON_FP32)):
+        s = bd.Sampler(probs, precision=prec, max_sweeps=8, stream=stream.cuda_stream)
+        s.sweep(1)
+        s.sync()
+        ms = timed_sweeps(s, 1, stream, torch)
+        if name == "fp64":
+            kms, nl = kernel_time(s, 1)
+            flops = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * q.n_chains *
+                        flops_per_update(q.L, q.S, photon_terms(q, s.get_mu(p, 0))) for p, q in enumerate(probs))
+            out["roofline"], out["bw_roofline"] = roofline(flops, kms, nl, upd, dev, peaks, "k_sweep<double>",
+                                                           fp64=True)
+        s.close()
+        out[name] = {"value": upd / (ms / 1e3), "unit": "pixel-updates/s", "ms_per_sweep": ms}
+    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def leg_widefield512(bd, stream, torch, dev, peaks, flush, checks, steps=3, sweeps=50):
+    prob = synth.widefield_512()
+    prob.burn_in = 0
+    prob.refresh_every = sweeps
+    Ho, Wo = prob.object_shape()
+    s = bd.Sampler(prob, precision=bd.BDECON_FP32, max_sweeps=(steps + 2) * sweeps + 8, stream=stream.cuda_stream)
+    s.sweep(sweeps)
+    s.sync()
+    ms = 0.0
+    for _ in range(steps):
+        flush()
+        ms += timed_sweeps(s, sweeps, stream, torch)
+    kms, nl = kernel_time(s, sweeps)
+    nt = photon_terms(prob, s.get_mu())
+    upd_launch = Ho * Wo * sweeps
+    rf, bw = roofline(flops_per_update(prob.L, prob.S, nt) * upd_launch, kms, nl, upd_launch, dev, peaks,
+                      "k_sweep<float> one-team form")
+    rho, t = s.get_state()
+    checks.append(dict(leg="widefield_512", what=f"float chain, trace after sweep {t}", prob=prob, rho=rho,
+                       trace=float(s.trace()[-1])))
+    out = {"workload": "512x512 sCMOS frame, PSF sigma 1.2 px on 17x17, 1 chain, refresh every 50, L2 flushed "
+                       "between steps", "plan": s.get_plan(),
+           "fp32": {"value": Ho * Wo * sweeps * steps / (ms / 1e3), "unit": "pixel-updates/s",
+                    "ms_per_sweep": ms / (steps * sweeps)},
+           "roofline": rf, "bw_roofline": bw, "mean_photon_terms": nt,
+           "acceptance": float(s.accept_counts()[-sweeps:].sum() / (sweeps * Ho * Wo))}
+    s.close()
+    s64 = bd.Sampler(prob, precision=bd.BDECON_FP64, max_sweeps=32, stream=stream.cuda_stream)
+    s64.sweep(2)
+    s64.sync()
+    flush()
+    ms64 = timed_sweeps(s64, 10, stream, torch)
+    s64.close()
+    out["fp64"] = {"value": Ho * Wo * 10 / (ms64 / 1e3), "unit": "pixel-updates/s", "ms_per_sweep": ms64 / 10}
+    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def leg_widefield64(bd, stream, torch):
+    """The plain double sampler on the 64x64 frame, 200 sweeps (and a 10-sweep
+    chain kept for the oracle comparison)."""
+    prob = synth.widefield_64()
+    Ho, Wo = prob.object_shape()
+    out = {"workload": "64x64 frame, 12 blobs + 3 lines, PSF sigma 1.5 px on 9x9, 1 chain, 200 sweeps"}
+    for name, prec in (("fp64", bd.BDECON_FP64), ("fp32", bd.BDECON_FP32)):
+        s = bd.Sampler(prob, precision=prec, max_sweeps=208, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        ms = timed_sweeps(s, 200, stream, torch)
+        s.close()
+        out[name] = {"value": Ho * Wo * 200 / (ms / 1e3), "unit": "pixel-updates/s", "ms_per_sweep": ms / 200}
+    s = bd.Sampler(prob, precision=bd.BDECON_FP64, max_sweeps=16, flags=bd.FLAG_ACCEPT_LOG,
+                   stream=stream.cuda_stream)
+    s.sweep(10)
+    s.sync()
+    exact = dict(sweeps=10, acc=s.accept_log(), rho=s.get_state()[0], trace=s.trace())
+    s.close()
+    return out, (prob, exact)
+
+
+def leg_lowsnr2048(bd, stream, torch, dev, peaks, checks):
+    prob = synth.lowsnr_2048()
+    Ho, Wo = prob.object_shape()
+    upd = Ho * Wo * prob.n_chains
+    out = {"workload": "2048x2048 low-SNR frame, peak 5 / background 1 photons, PSF sigma 4 px on 31x31, "
+                       "sCMOS maps, 4 chains, double refresh every 50 sweeps"}
+    s = bd.Sampler(prob, precision=bd.BDECON_FP32, max_sweeps=32, stream=stream.cuda_stream)
+    s.sweep(1)
+    s.sync()
+    ms = timed_sweeps(s, 5, stream, torch)
+    kms, nl = kernel_time(s, 2)
+    nt = photon_terms(prob, s.get_mu(0, 0))
+    out["roofline"], out["bw_roofline"] = roofline(flops_per_update(prob.L, prob.S, nt) * upd * 2, kms, nl,
+                                                   upd * 2, dev, peaks, "k_sweep<float>")
+    out["plan"] = s.get_plan()
+    out["fp32"] = {"value": upd * 5 / (ms / 1e3), "unit": "pixel-updates/s", "ms_per_sweep": ms / 5}
+    rho, t = s.get_state(0, 0)
+    checks.append(dict(leg="lowsnr_2048", what=f"float chain 0, trace after sweep {t}", prob=prob, rho=rho,
+                       trace=float(s.trace(0, 0)[-1])))
+    s.close()
+    s64 = bd.Sampler(prob, precision=bd.BDECON_FP64, max_sweeps=4, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    ms64 = timed_sweeps(s64, 1, stream, torch)
+    s64.close()
+    out["fp64"] = {"value": upd / (ms64 / 1e3), "unit": "pixel-updates/s", "ms_per_sweep": ms64}
+    out["fp32_over_fp64"] = out["fp32"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def run_serving(bd, precision, n_jobs=8, sweeps=500, rate=20.0, budget_gb=120):
     """The serving form: deconvolution jobs (filament frames, sides
     log-uniform in 128..2048 rounded to 32, PSF sigma U[1, 4] px, sCMOS maps,
-    one chain, float sweeps with a double refresh every 50, burn-in 250)
-    arrive as a Poisson stream of the given rate and are submitted to the
-    library's serving loop, which admits them under a device-memory budget
-    and sweeps all running jobs in shared launches.  The first n_jobs
-    arrivals of the stream are served; latency = finish - arrival."""
-    from paper_2411_00991_gb300 import bdecon
+    one chain, refresh every 50, burn-in 250) arrive as a Poisson stream of
+    the given rate and are submitted to the library's serving loop, which
+    admits them under a device-memory budget and sweeps all running jobs in
+    shared launches.  The first n_jobs arrivals are served; latency = finish
+    - arrival."""
     ta, sides, sig = synth.serving_arrivals(n_jobs, rate=rate, seed=4)
     jobs = [synth.serving_job(int(sides[k]), float(sig[k]), seed=1000 + k) for k in range(n_jobs)]
+    for q in jobs:
+        q.burn_in = min(q.burn_in, sweeps // 2)
     upd = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * q.n_chains * sweeps for q in jobs)
-    h2d = sum(q.image.nbytes + np.asarray(q.offset).nbytes + np.asarray(q.var).nbytes + q.psf.nbytes for q in jobs)
-    d2h = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * 8 for q in jobs)
-    srv = bdecon.Server(mem_budget=int(budget_gb) << 30, max_jobs=64, segment_sweeps=25,
-                        precision=bdecon.BDECON_FP32)
+    srv = bd.Server(mem_budget=int(budget_gb) << 30, max_jobs=64, segment_sweeps=25, precision=precision)
     t0 = time.perf_counter()
     ids = []
     for k, q in enumerate(jobs):
@@ -245,7 +444,7 @@ def run_serving(n_jobs=8, sweeps=500, rate=20.0, budget_gb=120):
     wall = time.perf_counter() - t0
     stats = srv.stats()
     srv.close()
-    lat = np.array([r[1][2] - (r[1][0]) for r in res])
+    lat = np.array([r[1][2] - r[1][0] for r in res])
     for m, _ in res:
         assert np.isfinite(m).all()
     return dict(value=upd / wall, unit="pixel-updates/s", jobs=n_jobs, sweeps_per_job=sweeps,
@@ -253,14 +452,14 @@ def run_serving(n_jobs=8, sweeps=500, rate=20.0, budget_gb=120):
                 memory_budget_gb=budget_gb, wall_s=wall, jobs_per_s=n_jobs / wall,
                 latency_p50_s=float(np.percentile(lat, 50)), latency_p99_s=float(np.percentile(lat, 99)),
                 queue_wait_p50_s=float(np.percentile([r[1][1] - r[1][0] for r in res], 50)),
-                segments=stats["segments"], h2d_bytes=int(h2d), d2h_bytes=int(d2h))
+                segments=stats["segments"])
 
 
 # ---------------------------------------------------------------- our arm --
 def run_ours(args):
     import torch
     import torch.distributed as dist
-    from paper_2411_00991_gb300 import bdecon
+    from paper_2411_00991_gb300 import bdecon as bd
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -269,37 +468,32 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    prob = synth.widefield_512()
-    prob.seed = prob.seed + 7919 * rank             # weak scaling: one independent chain per rank
-    W, K, S = args.warmup, args.steps, SWEEPS_PER_STEP
-    prob.burn_in = W * S                            # every timed sweep enters the running mean
-    prob.refresh_every = S
-    Ho, Wo = prob.object_shape()
-    upd_per_step = Ho * Wo * prob.n_chains * S
     stream = torch.cuda.current_stream(dev)
-    total_sweeps = (W + K) * S + 8
+    peaks = _peaks()
+    W, K, S = args.warmup, args.steps, SWEEPS_PER_STEP
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def l2_flush():
-        flush.fill_(1.0)
-
-    s = bdecon.Sampler(prob, precision=bdecon.BDECON_FP32, max_sweeps=total_sweeps,
-                       stream=stream.cuda_stream)
+    # ---- headline: the batched float form
+    probs = batch_problems(rank)
+    upd_sweep = obj_updates(probs)
+    ws_bytes = bd.Sampler.workspace_size(probs, bd.BDECON_FP32, (W + K + 4) * S + 8)
+    s = bd.Sampler(probs, precision=bd.BDECON_FP32, max_sweeps=(W + K + 4) * S + 8, stream=stream.cuda_stream)
+    s.sweep(1)
+    s.sync()
+    t = time.perf_counter()
+    tune = s.autotune(trial_sweeps=1)
+    tune_s = time.perf_counter() - t
+    s.set_graph(True)
+    s.sweep(S - 1)                      # align the sweep counter with the refresh period
     for _ in range(W):
         s.sweep(S)
     s.sync()
-    s.set_timing(True)
-    s.sweep_kernel_time()
     n0 = s.launch_count()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    evs = [_events(torch) for _ in range(K)]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for k in range(K):
-            l2_flush()
             evs[k][0].record(stream)
             s.sweep(S)
             evs[k][1].record(stream)
@@ -307,106 +501,73 @@ def run_ours(args):
     s.sync()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     launches = s.launch_count() - n0
-    kms, klaunch = s.sweep_kernel_time()
-    mu = s.get_mu()
-    tr = s.trace()
-    acc = s.accept_counts()
-    plan = s.get_plan()
-    s.close()
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * upd_per_step * K / (ms / 1e3)
-
-    # plain double sampler on the same frame (fewer sweeps: it is ~50x slower)
-    fp64 = None
-    if not args.no_fp64 and rank == 0:
-        s64 = bdecon.Sampler(prob, precision=bdecon.BDECON_FP64, max_sweeps=4 * S, stream=stream.cuda_stream)
-        s64.sweep(2)
-        s64.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n64 = args.fp64_sweeps
-        l2_flush()
-        e0.record(stream)
-        s64.sweep(n64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        s64.sync()
-        t64 = e0.elapsed_time(e1)
-        s64.close()
-        fp64 = dict(value=Ho * Wo * n64 / (t64 / 1e3), unit="pixel-updates/s", sweeps=n64,
-                    ms_per_sweep=t64 / n64)
-
-    # end to end through the C ABI from host buffers
-    e2e = None
-    if rank == 0:
-        ep = synth.widefield_512()
-        ep.burn_in = S // 2
-        ep.refresh_every = S
-        h2d = ep.image.nbytes + np.asarray(ep.offset).nbytes + np.asarray(ep.var).nbytes + ep.psf.nbytes
-        d2h = Ho * Wo * 8
-        ke = min(K, 3)
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        for _ in range(ke):
-            se = bdecon.Sampler(ep, precision=bdecon.BDECON_FP32, max_sweeps=S + 4, stream=stream.cuda_stream)
-            se.sweep(S)
-            mean = se.posterior_mean()
-            se.close()
-        dt = (time.perf_counter() - t) / ke
-        assert np.isfinite(mean).all()
-        e2e = dict(value=upd_per_step / dt, unit="pixel-updates/s", h2d_bytes_per_step=int(h2d),
-                   d2h_bytes_per_step=int(d2h), ms_per_step=dt * 1e3)
-
-    # the photon-count augmented float sampler on the same frame (same target)
-    augmented = None
-    if rank == 0 and not args.no_fp64:
-        pa = synth.widefield_512()
-        pa.burn_in = 0
-        pa.refresh_every = S
-        pa.augmented = True
-        sa = bdecon.Sampler(pa, precision=bdecon.BDECON_FP32, max_sweeps=4 * S, stream=stream.cuda_stream)
-        sa.sweep(S)
-        sa.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l2_flush()
-        e0.record(stream)
-        sa.sweep(2 * S)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        sa.sync()
-        ta = e0.elapsed_time(e1)
-        acc_a = float(sa.accept_counts()[-2 * S:].sum() / (2 * S * Ho * Wo))
-        sa.close()
-        augmented = dict(value=Ho * Wo * 2 * S / (ta / 1e3), unit="pixel-updates/s", sweeps=2 * S,
-                         ms_per_sweep=ta / (2 * S), acceptance=acc_a)
-
-    batched = None
-    if rank == 0 and not args.no_batch:
-        batched = run_batched(stream.cuda_stream)
-    serving = None
-    if rank == 0 and not args.no_serve:
-        serving = run_serving(n_jobs=args.serve_jobs)
+        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * upd_sweep * S * K / (ms / 1e3)
+    plans = sorted({json.dumps(s.get_plan(p), sort_keys=True) for p in range(len(probs))})
 
     if rank != 0:
+        s.close()
         if world > 1:
             dist.destroy_process_group()
         return
 
-    peaks = _peaks()
-    fpu, nterms = flops_per_update(prob, mu)
-    launch_ms = kms / max(klaunch, 1)
-    upd_per_launch = Ho * Wo * prob.n_chains * S        # one launch covers one refresh period
-    ach_tflops = fpu * upd_per_launch / (launch_ms / 1e3) / 1e12
-    clocks = clk.summary()
-    peak_tflops = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
-    alg_bytes_per_update = 68.0
-    # DRAM bytes (read + write) of one sweep-kernel launch on this frame from an ncu
-    # capture of the same kernel (a 2-sweep launch): the state is L2-resident, so the
-    # DRAM traffic is the first touch of the state and does not grow with sweeps
-    traffic = 17.20e6
-    ach_gbs = alg_bytes_per_update * upd_per_launch / (launch_ms / 1e3) / 1e9
+    # kernel-only time of one step (plain launches, one per launch group and segment)
+    s.set_graph(False)
+    kms, nl = kernel_time(s, S)
+    nts = [photon_terms(q, s.get_mu(p, 0)) for p, q in enumerate(probs)]
+    flops = S * sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * q.n_chains * flops_per_update(q.L, q.S, nt)
+                    for q, nt in zip(probs, nts))
+    rf, bw = roofline(flops, kms, nl, upd_sweep * S, dev, peaks, "k_sweep<float> (batched launch groups)")
+    checks = []
+    order = np.argsort([q.H for q in probs])
+    for p in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+        rho, t = s.get_state(p, 0)
+        checks.append(dict(leg="batched", what=f"frame {p} ({probs[p].H}x{probs[p].W}, L {probs[p].L}) chain 0, "
+                                               f"trace after sweep {t}", prob=probs[p], rho=rho,
+                           trace=float(s.trace(p, 0)[-1])))
+    acc = sum(float(s.accept_counts(p, c)[-S:].sum()) for p, q in enumerate(probs) for c in range(q.n_chains))
+    s.close()
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = [_pinned_copy(q, torch) for q in probs]
+        h2d = sum(np.asarray(getattr(q, k)).nbytes for q in pin for k in ("image", "offset", "var", "psf")
+                  if not np.isscalar(getattr(q, k)))
+        d2h = sum((q.H + 2 * q.R) * (q.W + 2 * q.R) * 8 for q in pin)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        se = bd.Sampler(pin, precision=bd.BDECON_FP32, max_sweeps=S + 4, stream=stream.cuda_stream)
+        se.sweep(S)
+        means = [se.posterior_mean(p) for p in range(len(pin))]
+        se.close()
+        dt = time.perf_counter() - t
+        assert all(np.isfinite(m).all() for m in means)
+        e2e = dict(value=upd_sweep * S / dt, unit="pixel-updates/s", h2d_bytes_per_step=int(h2d),
+                   d2h_bytes_per_step=int(d2h), ms_per_step=dt * 1e3,
+                   step="create from pinned host buffers + 10 sweeps + posterior means of all 64 frames")
+
+    flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    legs = {}
+    exact64 = None
+    if not args.no_legs:
+        legs["fp64_plain"] = leg_fp64_batch(bd, stream, torch, dev, peaks, rank)
+        legs["widefield_512"] = leg_widefield512(bd, stream, torch, dev, peaks, flush, checks)
+        legs["widefield_64"], exact64 = leg_widefield64(bd, stream, torch)
+        legs["lowsnr_2048"] = leg_lowsnr2048(bd, stream, torch, dev, peaks, checks)
+    if not args.no_serve:
+        legs["serving"] = {"fp32": run_serving(bd, bd.BDECON_FP32, n_jobs=args.serve_jobs),
+                           "fp64": run_serving(bd, bd.BDECON_FP64, n_jobs=args.serve_jobs, sweeps=5)}
+        legs["serving"]["note"] = ("the double arm serves the same arrival stream with 5 sweeps per job "
+                                   "(500 would take ~1 h): compare throughput, not latency")
+
     line = {
         "metric": METRIC,
         "value": value,
@@ -419,31 +580,29 @@ def run_ours(args):
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded filament+blob object, Poisson photons, sCMOS maps)",
-        "config": {"workload": "widefield 512x512 frame, Gaussian PSF sigma 1.2 px on 17x17, sCMOS offset "
-                               "N(100,2) / variance Gamma(2,1) maps, gain 2.1, 1 chain, float sweeps with "
-                               "double refresh every 50 sweeps",
-                   "sweeps_per_step": S, "object_pixels": Ho * Wo, "chains_per_gpu": prob.n_chains,
-                   "l2": "flushed (256 MB write) between timed steps", "plan": plan},
+        "data": "synthetic (seeded filament+blob objects, Poisson photons, Gaussian read noise)",
+        "config": {"workload": "batched: 64 frames, sides uniform from {128,256,384,512,768,1024}, Gaussian PSF "
+                               "sigma U[1,4] px on 2 ceil(3 sigma)+1, peak log-U[3,200] photons, background 1, "
+                               "gain 2.0 / offset 100 / read sd 1.6, 4 chains each; float sweeps, double refresh "
+                               "every 10 sweeps; autotuned launch shapes, CUDA graph",
+                   "sweeps_per_step": S, "updates_per_sweep": upd_sweep, "images": len(probs),
+                   "chains": sum(q.n_chains for q in probs), "workspace_bytes": int(ws_bytes),
+                   "l2": "inputs larger than L2 (chain state ~%.1f GB vs 129 MB), no flush" % (ws_bytes / 1e9),
+                   "plans": [json.loads(x) for x in plans],
+                   "autotune": dict(one_launch=tune["one_launch"], trial_ms_per_sweep=tune["ms_per_sweep"],
+                                    seconds=tune_s)},
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "clocks": clocks,
-        "roofline": {"bound": "alu", "kernel": "k_sweep<float>", "achieved": ach_tflops,
-                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": ach_tflops / peak_tflops,
-                     "traffic": traffic, "flops_per_update": fpu, "mean_photon_terms": nterms,
-                     "launch_ms": launch_ms, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"},
-        "bw_roofline": {"achieved": ach_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                        "frac": ach_gbs / peaks["hbm_gbs"], "bytes_per_update": alg_bytes_per_update,
-                        "peak_source": peaks["source"]},
-        "fp64": fp64,
-        "augmented": augmented,
-        "batched": batched,
-        "serving": serving,
-        "acceptance": float(acc[-K * S:].sum() / (K * S * Ho * Wo)),
-        "trace_last": float(tr[-1]),
+        "clocks": clk.summary(),
+        "roofline": rf,
+        "bw_roofline": bw,
+        "mean_photon_terms": float(np.average(nts, weights=[q.L * q.L for q in probs])),
+        "acceptance": acc / (upd_sweep * S),
+        "legs": legs,
     }
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(sweeps=1)
+        line["cpu_baseline"] = cpu_baseline()
+        line["oracle_error"] = oracle_errors(checks, exact64)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -456,14 +615,12 @@ def run_reference(args):
         return
     W, K = args.warmup, args.steps
     vals = []
-    cores = None
+    r = None
     for k in range(W + K):
-        r = cpu_baseline(sweeps=1)
-        cores = r["cores"]
+        r = cpu_baseline()
         if k >= W:
             vals.append(r["value"])
     v = float(np.mean(vals))
-    side = CROP + 16
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -472,33 +629,47 @@ def run_reference(args):
         "n_gpus": world,
         "steps": K,
         "warmup": W,
-        "ms_per_step": side * side * cores / v * 1e3,
+        "ms_per_step": (CROP + 24) ** 2 * r["cores"] / v * 1e3,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64",
-        "data": "synthetic (seeded filament+blob object, Poisson photons, sCMOS maps)",
-        "config": {"workload": "widefield 512x512 frame, Gaussian PSF sigma 1.2 px on 17x17, sCMOS maps, "
-                               "gain 2.1, 1 chain; reference = the C oracle on a 128x128 crop, one chain "
-                               "per host core, 1 sweep per step"},
-        "cpu_baseline": {"value": v, "unit": "pixel-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{CROP}x{CROP} crop of the 512x512 frame, 1 sweep per core per step"},
+        "data": "synthetic (seeded filament+blob objects, Poisson photons, Gaussian read noise)",
+        "config": {"workload": "batched: 64 uneven frames x 4 chains (as the GPU arm); reference = the C oracle, "
+                               f"one sweep of a {CROP}x{CROP} crop of batch frame k per host core k per step"},
+        "cpu_baseline": {"value": v, "unit": "pixel-updates/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": r["sample"]},
         "e2e": {"value": v, "unit": "pixel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
 def run_profile(args):
-    """Small case for ncu: the same frame and plan, one warm-up launch and then
-    one sweep-kernel launch of --profile sweeps (no refresh inside it)."""
+    """Small cases for ncu: --profile N runs one launch of N sweeps of the
+    512x512 frame after a warm-up launch; --profile-batch L runs two sweeps of
+    the batch frames whose PSF side is L (one launch group)."""
     import torch
-    from paper_2411_00991_gb300 import bdecon
+    from paper_2411_00991_gb300 import bdecon as bd
+    st = torch.cuda.current_stream().cuda_stream
+    if args.profile_batch:
+        # the batch frames of this PSF side with many updates per class step
+        # (chains x patches >= 2048): one launch group
+        probs = [q for q in batch_problems() if q.L == args.profile_batch and
+                 q.n_chains * math.ceil((q.H + 2 * q.R) / q.S) * math.ceil((q.W + 2 * q.R) / q.S) >= 2048]
+        s = bd.Sampler(probs, precision=bd.BDECON_FP32, max_sweeps=16, stream=st)
+        s.sweep(1)
+        s.sync()
+        s.sweep(1)
+        s.sync()
+        print(json.dumps({"profile_batch_L": args.profile_batch, "images": len(probs), "sides": [q.H for q in probs],
+                          "updates_per_sweep": obj_updates(probs), "plan": s.get_plan()}))
+        s.close()
+        return
     prob = synth.widefield_512()
     prob.burn_in = 0
     prob.refresh_every = 0
-    prec = bdecon.BDECON_FP64 if args.profile_fp64 else bdecon.BDECON_FP32
-    s = bdecon.Sampler(prob, precision=prec, max_sweeps=args.profile + 8,
-                       stream=torch.cuda.current_stream().cuda_stream)
+    prec = bd.BDECON_FP64 if args.profile_fp64 else bd.BDECON_FP32
+    s = bd.Sampler(prob, precision=prec, max_sweeps=args.profile + 8, stream=st)
     s.sweep(2)
     s.sync()
     s.sweep(args.profile)
@@ -510,19 +681,19 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="headline only (no per-config legs)")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=8)
-    ap.add_argument("--fp64-sweeps", type=int, default=20)
     ap.add_argument("--profile", type=int, default=0, help="ncu mode: one launch of this many sweeps")
     ap.add_argument("--profile-fp64", action="store_true")
+    ap.add_argument("--profile-batch", type=int, default=0, help="ncu mode: the batch frames of this PSF side")
     args = ap.parse_args()
-    if args.profile:
+    if args.profile or args.profile_batch:
         run_profile(args)
         return
     if args.warmup < 3:

@@ -310,25 +310,27 @@ def batch_uneven(n_images=64, seed0=3000, sides=(128, 256, 384, 512, 768, 1024),
     """Batch of uneven frames: side uniform from ``sides``, PSF sigma U[1, 4] px
     with support 2*ceil(3 sigma)+1, peak log-U[3, 200], background 1, camera
     scalars gain 2.0 / offset 100 / read sd 1.6; 4 chains each."""
-    out = []
-    for i in range(n_images):
-        rng = np.random.default_rng(seed0 + i)
-        side = int(rng.choice(sides))
-        sigma = float(rng.uniform(1.0, 4.0))
-        L = 2 * int(math.ceil(3 * sigma)) + 1
-        peak = float(math.exp(rng.uniform(math.log(3.0), math.log(200.0))))
-        R = L // 2
-        shape = (side + 2 * R, side + 2 * R)
-        frac = (side / 512.0) ** 2
-        struct = _filaments(shape, max(1, int(200 * frac)), 20, 200, rng) + \
-            _blobs(shape, max(1, int(50 * frac)), 1.0, 3.0, 0.3, 1.0, rng)
-        truth = _scale(struct, peak, 1.0)
-        psf = gaussian_psf(sigma, L)
-        img = simulate_frame(truth, psf, 2.0, 100.0, 1.6 ** 2, rng)
-        out.append(Problem(image=img, psf=psf, gain=2.0, offset=100.0, var=1.6 ** 2,
-                           n_chains=n_chains, seed=seed0 + i, refresh_every=50,
-                           burn_in=250, truth=truth, name=f"batch{i}_{side}_L{L}"))
-    return out
+    return [batch_frame(i, seed0, sides, n_chains) for i in range(n_images)]
+
+
+def batch_frame(i, seed0=3000, sides=(128, 256, 384, 512, 768, 1024), n_chains=4) -> Problem:
+    """Frame i of ``batch_uneven`` alone (each frame depends only on seed0 + i)."""
+    rng = np.random.default_rng(seed0 + i)
+    side = int(rng.choice(sides))
+    sigma = float(rng.uniform(1.0, 4.0))
+    L = 2 * int(math.ceil(3 * sigma)) + 1
+    peak = float(math.exp(rng.uniform(math.log(3.0), math.log(200.0))))
+    R = L // 2
+    shape = (side + 2 * R, side + 2 * R)
+    frac = (side / 512.0) ** 2
+    struct = _filaments(shape, max(1, int(200 * frac)), 20, 200, rng) + \
+        _blobs(shape, max(1, int(50 * frac)), 1.0, 3.0, 0.3, 1.0, rng)
+    truth = _scale(struct, peak, 1.0)
+    psf = gaussian_psf(sigma, L)
+    img = simulate_frame(truth, psf, 2.0, 100.0, 1.6 ** 2, rng)
+    return Problem(image=img, psf=psf, gain=2.0, offset=100.0, var=1.6 ** 2,
+                   n_chains=n_chains, seed=seed0 + i, refresh_every=50,
+                   burn_in=250, truth=truth, name=f"batch{i}_{side}_L{L}")
 
 
 def serving_arrivals(n_jobs=300, rate=20.0, seed=4, lo=128, hi=2048):
