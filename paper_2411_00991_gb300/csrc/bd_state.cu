@@ -11,6 +11,9 @@
 // not depend on the launch plan of the sweep kernel.
 #include <cmath>
 
+#include <atomic>
+#include <mutex>
+
 #include "bd_device.cuh"
 
 namespace bd {
@@ -273,13 +276,38 @@ __global__ void __launch_bounds__(kRedThreads) k_refresh_mu(Image im, Chain ch, 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_refresh_spec(Image im, Chain ch, double* part_lp, int write)
 {
+    // one block per patch: its half spectrum by the 2-D DFT taken as two
+    // 1-D transforms (rows, then columns), O(ph pw (ph + pw)) instead of
+    // O((ph pw)^2) for the direct sum, in double in shared memory:
+    //   Y[u][l] = sum_v x[u][v] exp(-2 pi i l v / pw),
+    //   X[k][l] = sum_u Y[u][l] exp(-2 pi i k u / ph)
+    extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ double sh[kRedThreads];
     const int p = blockIdx.x;
     const int pi = p / im.npj, pj = p % im.npj;
     const Shape& sp = im.shape[shape_index(im, pi, pj)];
+    const int ph = sp.ph, pw = sp.pw, n = ph * pw;
+    double* x = reinterpret_cast<double*>(dyn);                    // [ph][pw]
+    double2* Y = reinterpret_cast<double2*>(dyn) + (n + 1) / 2;     // [ph][pw]
     const T* rho = reinterpret_cast<const T*>(ch.rho) + (size_t)pi * im.S * im.Wo + pj * im.S;
     const double2* twh = reinterpret_cast<const double2*>(im.tw64) + sp.twh_off;
     const double2* tww = reinterpret_cast<const double2*>(im.tw64) + sp.tww_off;
+    for (int e = threadIdx.x; e < n; e += kRedThreads) {
+        const int u = e / pw, v = e - (e / pw) * pw;
+        x[e] = (double)rho[(size_t)u * im.Wo + v];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n; e += kRedThreads) {
+        const int u = e / pw, l = e - (e / pw) * pw;
+        double re = 0.0, imv = 0.0;
+        for (int v = 0; v < pw; ++v) {
+            const double2 w = tww[(l * v) % pw];
+            re += x[u * pw + v] * w.x;
+            imv += x[u * pw + v] * w.y;
+        }
+        Y[e] = make_double2(re, imv);
+    }
+    __syncthreads();
     using T2 = typename Vec2<T>::type;
     T2* spec = reinterpret_cast<T2*>(ch.spec) + im.patch_off[p];
     double sl = 0.0, sm = 0.0;
@@ -287,15 +315,11 @@ __global__ void __launch_bounds__(kRedThreads) k_refresh_spec(Image im, Chain ch
         const int kl = im.ent_kl[sp.ent_off + e];
         const int k = kl >> 16, l = kl & 0xffff;
         double re = 0.0, imv = 0.0;
-        for (int u = 0; u < sp.ph; ++u) {
-            const double2 eh = twh[(k * u) % sp.ph];
-            for (int v = 0; v < sp.pw; ++v) {
-                const double2 ew = tww[(l * v) % sp.pw];
-                const double wr = eh.x * ew.x - eh.y * ew.y, wi = eh.x * ew.y + eh.y * ew.x;
-                const double x = (double)rho[(size_t)u * im.Wo + v];
-                re += x * wr;
-                imv += x * wi;
-            }
+        for (int u = 0; u < ph; ++u) {
+            const double2 w = twh[(k * u) % ph];
+            const double2 y = Y[u * pw + l];
+            re += y.x * w.x - y.y * w.y;
+            imv += y.x * w.y + y.y * w.x;
         }
         if (write) {
             T2 X;
@@ -332,7 +356,17 @@ void launch_refresh(const Image& im, const Chain& ch, double* scratch, int write
     double* part_ll = scratch;
     double* part_lp = scratch + nblk;
     k_refresh_mu<T><<<nblk, kRedThreads, 0, st>>>(im, ch, part_ll, write_state, err);
-    k_refresh_spec<T><<<im.n_patches, kRedThreads, 0, st>>>(im, ch, part_lp, write_state);
+    // the patch and its row transforms in shared memory (24 bytes per patch pixel)
+    const size_t smem = 8 * (size_t)(((size_t)im.S * im.S + 1) / 2 * 2) + 16 * (size_t)im.S * im.S;
+    static std::atomic<size_t> limit{48 * 1024};   // the dynamic shared-memory limit only grows
+    static std::mutex mu;
+    if (smem > limit.load()) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (smem > limit.load() &&
+            cudaFuncSetAttribute(k_refresh_spec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess)
+            limit.store(smem);
+    }
+    k_refresh_spec<T><<<im.n_patches, kRedThreads, smem, st>>>(im, ch, part_lp, write_state);
     k_refresh_total<<<1, kRedThreads, 0, st>>>(part_ll, nblk, part_lp, im.n_patches, out_logpost, out_index);
     *launches += 3;
 }

@@ -274,10 +274,28 @@ void describe(ProbHost& ph)
     ph.spec_len = off;
 }
 
+// Blocks per SM of the sweep kernel's forms for this launch shape, memoized:
+// the planner asks at every tile-growth step, and the answer depends only on
+// the device, the precision, the block size, the shared memory and the form.
 int occupancy(int prec, int threads, size_t smem, bool aug, bool fine, int stg)
 {
-    return prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug, fine, stg)
-                               : sweep_blocks_per_sm<double>(threads, smem, aug, fine, stg);
+    static std::mutex mu;
+    static std::map<std::vector<long long>, int> memo;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const std::vector<long long> key = {dev, prec, threads, (long long)smem, aug ? 1 : 0, fine ? 1 : 0, stg};
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+    }
+    const int n = prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug, fine, stg)
+                                      : sweep_blocks_per_sm<double>(threads, smem, aug, fine, stg);
+    if (n > 0) {
+        std::lock_guard<std::mutex> lock(mu);
+        memo[key] = n;
+    }
+    return n;
 }
 
 constexpr size_t kMaxSmem = 227 * 1024;
