@@ -127,7 +127,8 @@ __global__ void k_setup_tw(int n, double* tw64, float* tw32)
 __global__ void __launch_bounds__(kRedThreads) k_setup_alpha(int L, const double* K64, int ph, int pw,
                                                             const int* ent_kl, int nhalf, double* kw,
                                                             double* mag, double* wa64, double* m64,
-                                                            float* wa32, float* m32)
+                                                            float* wa32, float* m32, const double2* twh,
+                                                            const double2* tww)
 {
     __shared__ double sh[kRedThreads];
     const int R = L / 2, n = ph * pw;
@@ -143,15 +144,17 @@ __global__ void __launch_bounds__(kRedThreads) k_setup_alpha(int L, const double
     double part = 0.0;
     for (int idx = threadIdx.x; idx < n; idx += kRedThreads) {
         const int k = idx / pw, l = idx % pw;
+        // exp(-2 pi i (k u / ph + l v / pw)) from the twiddle tables of the two sides
         double re = 0.0, im = 0.0;
-        for (int u = 0; u < ph; ++u)
+        for (int u = 0; u < ph; ++u) {
+            const double2 eh = twh[(k * u) % ph];
             for (int v = 0; v < pw; ++v) {
-                const double fr = (double)((k * u) % ph) / ph + (double)((l * v) % pw) / pw;
-                double s, c;
-                sincospi(2.0 * fr, &s, &c);
-                re += kw[u * pw + v] * c;
-                im -= kw[u * pw + v] * s;
+                const double2 ew = tww[(l * v) % pw];
+                const double x = kw[u * pw + v];
+                re += x * (eh.x * ew.x - eh.y * ew.y);
+                im += x * (eh.x * ew.y + eh.y * ew.x);
             }
+        }
         mag[idx] = hypot(re, im);
         part += mag[idx];
     }
@@ -214,7 +217,9 @@ void launch_setup(const Image& im, const Image* d_im, const float* w, const floa
                                                  mag, const_cast<double*>(im.ent_wa64) + sh.ent_off,
                                                  const_cast<double*>(im.ent_m64) + sh.ent_off,
                                                  const_cast<float*>(im.ent_wa32) + sh.ent_off,
-                                                 const_cast<float*>(im.ent_m32) + sh.ent_off);
+                                                 const_cast<float*>(im.ent_m32) + sh.ent_off,
+                                                 reinterpret_cast<const double2*>(im.tw64) + sh.twh_off,
+                                                 reinterpret_cast<const double2*>(im.tw64) + sh.tww_off);
         *launches += 3;
     }
 }
