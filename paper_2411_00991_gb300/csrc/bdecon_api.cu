@@ -52,6 +52,7 @@ struct ProbHost {
     size_t o_sum, o_sq, o_scr, o_samp, o_adapt;
     int samp_first = 0;         // first valid kept-object slot (after a resume)
     bool stage_ok = false;      // its chains carry TMA tensor maps for window staging
+    bool many = false;          // many independent updates per class step (its team chosen for throughput)
     size_t scr_doubles;
     int chain0;
 };
@@ -72,6 +73,7 @@ struct Group {
     bool solo = false;                 // every block: one patch, one team (a kernel form of its own)
     int stage = 0;                     // window staging by the TMA engine (a kernel form): 1 on, 0 off
     bool no_stage = true;              // window staging not allowed in this group's plan
+    bool many = false;                 // every problem has many updates per class step: two teams per block
     bool user_stage = false;           // no_stage set by the autotuner, not by the handle's setting
     int chain_off = 0, n_chains = 0;   // slice of the group-ordered chain table
 };
@@ -362,7 +364,10 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
 {
     int team = 32;
     for (const PlanItem* it : items) team = std::max(team, it->team);
-    g.threads = g.user_warps ? std::max(32 * g.warps, team) : team;
+    // default block: one update team; two when every problem has many updates
+    // per class step (measured: the autotuner's usual choice for such groups)
+    const int dflt = g.many && 2 * team <= 256 ? 2 * team : team;
+    g.threads = g.user_warps ? std::max(32 * g.warps, team) : dflt;
     g.warps = g.threads / 32;
     const int ts = precision == BDECON_FP32 ? 4 : 8;
     // window staging: float marginal camera-grid problems whose chains carry
@@ -523,6 +528,10 @@ void form_groups(bdecon_handle* h)
         }
         h->groups[gi].probs.push_back(k);
         h->prob_group[k] = gi;
+    }
+    for (auto& g : h->groups) {
+        g.many = true;
+        for (int k : g.probs) g.many = g.many && h->probs[k].many;
     }
 }
 
@@ -757,6 +766,7 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         im.spec_len = ph.spec_len;
         im.n_ent = (int)ph.ent_kl.size();
         im.team = problem_team(ph.Lc, ph.p.n_chains, ph.n_patches, ph.p.team_warps, h->precision == BDECON_FP32);
+        ph.many = ph.p.team_warps == 0 && (long long)ph.p.n_chains * ph.n_patches >= 2048;
         im.n_tw = ph.n_tw;
         im.max_nhalf = ph.max_nhalf;
         im.sample_every = ph.p.sample_every > 0 ? ph.p.sample_every : 1;
