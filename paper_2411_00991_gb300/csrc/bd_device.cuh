@@ -125,6 +125,18 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Barrier of the n threads (whole warps) of one of two update teams: named
+// barrier 1 or 2 (0 is the block-wide barrier of __syncthreads).  Orders the
+// team's shared- and global-memory accesses like __syncthreads does for the
+// block.  The ids are immediates, so a kernel reserves three barriers, not
+// the sixteen that an id held in a register would reserve (which costs
+// resident blocks per SM).
+__device__ __forceinline__ void team_bar2(int team, int n)
+{
+    if (team == 0) asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
+}
+
 // ------------------------------------------------------ memory ordering --
 // Fire-and-forget additions to a progress word.  Publishing by read-modify-
 // write keeps every word a reader can observe in observation order after the

@@ -538,6 +538,17 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
     // together (wide), else the whole warp draws the next one.  Not when a
     // sweep is a single round (S = 1 and one round), where the next update
     // revisits the pixel.
+    // Blocks of two update teams with several rounds per class step (tb):
+    // after the first round of a step the teams share nothing until the step
+    // ends -- their patches, windows, partial sums, proposal rings and staging
+    // buffers are their own -- so in those rounds each team synchronises alone
+    // (tsync, a named barrier per team; threads outside both teams take no
+    // part), a team does not wait for the other's slower round, and the block
+    // meets again at the step's end.  Other plans use block barriers throughout.
+    const bool tb = !SOLO && n_sub == 2 && rounds > 1;
+    auto tsync = [&]() {
+        if (in_team) team_bar2(g, NT);
+    };
     const int SR = S2 * rounds;   // rounds per sweep
     const bool ahead = SR > 1;
     const int pwarp = nwt > 1 ? 1 : 0;   // the drawing warp: not the one that polls the flags
@@ -793,10 +804,14 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                                              delta, muv, red2 + twarp * 4, lane, cq, cq2, true);
             }
             // a5: Metropolis-Hastings decision with the Hastings term of the log-space
-            // walk, taken from the round's partial sums as soon as every warp has
-            // written them -- before the neighbour wait, so that a rejected update
-            // (the common case) leaves only the wait and the publish after it
-            __syncthreads();
+            // walk, taken from the round's partial sums as soon as every warp of the
+            // team has written them -- before the neighbour wait, so that a rejected
+            // update (the common case) leaves only the wait and the publish after it.
+            // In the first round the whole block meets: every thread has then read
+            // the previous step's stale and abort flags, which the polling warp
+            // is about to overwrite
+            if (r == 0 || !tb) __syncthreads();
+            else tsync();
             T dL = 0, dP = 0;
             bool accept = false, nonfin = false;
             auto decide = [&]() {
@@ -853,15 +868,19 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // (the partial sums are not read after this barrier, so the next round
             // may overwrite them; writes of an accepted update need one more)
             // (one-team form: every thread took the same decision, so a plain
-            // barrier does)
+            // barrier does; team barriers: a team's decision is uniform in it)
+            const bool blk = r == 0 || !tb;
             int any_accept;
             if constexpr (SOLO) {
                 __syncthreads();
                 any_accept = active && accept ? 1 : 0;
-            } else {
+            } else if (blk) {
                 any_accept = __syncthreads_or(active && accept ? 1 : 0);
+            } else {
+                tsync();
+                any_accept = active && accept ? 1 : 0;
             }
-            if (s_abort) {
+            if (blk && s_abort) {
                 stage_drain();
                 return;
             }
@@ -950,7 +969,21 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                     sg[m] = sn < (T)1e-4 ? (T)1e-4 : sn > (T)4 ? (T)4 : sn;
                 }
             }
-            if (stale || any_accept) __syncthreads();
+            if (blk) {
+                if (stale || any_accept) __syncthreads();
+            } else if (any_accept) {
+                tsync();
+            }
+        }
+        // team barriers: the block meets before the sweep's end work and the
+        // publish (which must follow both teams' writes), and a team's failed
+        // copy wait (s_abort) is acted on here
+        if (tb) {
+            __syncthreads();
+            if (s_abort) {
+                stage_drain();
+                return;
+            }
         }
         if (c == S2 - 1) {
             // a7: after the sweep, add the object to the running sums (own
