@@ -11,8 +11,9 @@ accept/write, class schedule, running mean, refresh).  The chains' state
 (~5 GB) is far larger than L2, so no flush is needed between steps.
 
 e2e       the same metric through the C ABI from pinned host buffers: create
-          (H2D of the 64 frames, set-up, first refresh), one step of sweeps,
-          posterior means of every frame (D2H)
+          (H2D of the 64 frames, set-up, first refresh; the launch plan comes
+          from the library's tuning cache, filled by the headline's autotune),
+          one step of sweeps, posterior means of every frame (D2H)
 roofline  the sweep kernel against the plain-ALU peak (SMs x 128 FP32 lanes x
           2 x max SM clock), with the algorithmic work per update
           L^2 (4 n + 10) + 12 S^2 (n the photon counts carrying >= 2^-26 of a
@@ -548,7 +549,8 @@ def run_ours(args):
         assert all(np.isfinite(m).all() for m in means)
         e2e = dict(value=upd_sweep * S / dt, unit="pixel-updates/s", h2d_bytes_per_step=int(h2d),
                    d2h_bytes_per_step=int(d2h), ms_per_step=dt * 1e3,
-                   step="create from pinned host buffers + 10 sweeps + posterior means of all 64 frames")
+                   step="create from pinned host buffers (launch plan from the library's tuning cache, "
+                        "filled by the autotune above) + 10 sweeps + posterior means of all 64 frames")
 
     flush_buf = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 

@@ -315,6 +315,19 @@ bdecon_status bdecon_set_grouping(bdecon_handle* h, int32_t one_launch);
 bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* one_launch,
                               double* ms_per_sweep);
 
+/* Tuning cache (process-wide; no counterpart in the paper, which describes
+ * no implementation).  Each successful bdecon_autotune stores its choices
+ * (grouping; per group: warps per block, resident or streamed tile state,
+ * window staging) keyed by the device, the precision, the handle's staging
+ * setting and every problem's frame size, PSF side, stride, lattice factor,
+ * chain count, sampler and update team, in order.  A handle created later
+ * for the same key (bdecon_create, _batch_create, _create_in) starts with
+ * that plan instead of the automatic one; tiles are planned as usual.  A
+ * plan never changes a chain's results, only its speed.  enable 0 clears the
+ * cache and turns it off, 1 clears it and turns it on (the default).
+ * Thread-safe.                                                              */
+bdecon_status bdecon_set_tuning_cache(int32_t enable);
+
 bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int32_t* warps,
                               int32_t* tile_i, int32_t* tile_j);
 

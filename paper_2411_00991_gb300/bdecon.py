@@ -60,7 +60,8 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_server_submit", "bdecon_server_poll", "bdecon_server_wait", "bdecon_server_stats",
            "bdecon_server_stop", "bdecon_set_grouping", "bdecon_autotune", "bdecon_set_graph",
            "bdecon_posterior_std", "bdecon_posterior_cv", "bdecon_get_samples", "bdecon_posterior_quantiles",
-           "bdecon_get_steps", "bdecon_get_phi", "bdecon_set_staging", "bdecon_get_staging"]
+           "bdecon_get_steps", "bdecon_get_phi", "bdecon_set_staging", "bdecon_get_staging",
+           "bdecon_set_tuning_cache"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -116,6 +117,7 @@ def load(build_if_missing: bool = True):
         "bdecon_set_grouping": [H, i32],
         "bdecon_set_graph": [H, i32],
         "bdecon_autotune": [H, i32, C.POINTER(i32), dp],
+        "bdecon_set_tuning_cache": [i32],
         "bdecon_server_start": [C.POINTER(_ServerConfig), C.POINTER(vp)],
         "bdecon_server_submit": [vp, P, i32, C.POINTER(i64)],
         "bdecon_server_poll": [vp, i64, C.POINTER(i32), vp, vp, sz],
@@ -169,6 +171,18 @@ def _problem(pr, precision, max_sweeps, flags, keep) -> _Problem:
                     int(getattr(pr, "team_warps", 0)), int(getattr(pr, "sample_every", 0)),
                     int(getattr(pr, "n_samples", 0)), float(getattr(pr, "adapt_target", 0.0)),
                     int(getattr(pr, "subpixel", 1)))
+
+
+def set_tuning_cache(enable: bool = True) -> None:
+    """Clear the process-wide tuning cache and turn it on (default) or off.
+
+    While on, every successful Sampler.autotune stores its launch choices
+    keyed by the device, precision and problem shapes, and a Sampler created
+    later for the same shapes starts with them (results never depend on the
+    plan, only the speed does)."""
+    rc = load().bdecon_set_tuning_cache(int(bool(enable)))
+    if rc != 0:
+        raise RuntimeError("bdecon_set_tuning_cache failed (%d)" % rc)
 
 
 def log_posterior_static(H, W, image_ptr, L, psf_ptr, gain, offset, var, stride, rho_ptr, out_ptr,

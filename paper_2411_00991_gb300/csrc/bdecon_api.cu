@@ -682,6 +682,68 @@ bdecon_status check_device(bdecon_handle* h)
     return BDECON_OK;
 }
 
+struct TuneChoice {
+    int warps = 0;          // 0: the team's own
+    bool streamed = false;
+    bool staged = false;
+    double ms = 1e300;
+};
+
+// Tuning cache: the autotuner's choices, kept for the life of the process
+// and keyed by the device, the precision, the staging setting and every
+// problem's shape (frame, PSF side, stride, lattice, chains, sampler, team),
+// in order.  A handle created later for the same shapes starts with the
+// tuned plan instead of the automatic one.  A plan changes no chain (every
+// plan gives bit-identical results), only the speed.
+struct TuneEntry {
+    bool one_launch = false;
+    std::vector<TuneChoice> groups;
+};
+std::mutex g_tune_mu;
+std::map<std::vector<long long>, TuneEntry> g_tune_cache;
+bool g_tune_cache_on = true;
+
+std::vector<long long> tune_key(const bdecon_handle* h)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<long long> k = {dev, h->sms, h->precision, h->staging};
+    for (size_t q = 0; q < h->probs.size(); ++q) {
+        const ProbHost& ph = h->probs[q];
+        k.insert(k.end(), {ph.H, ph.W, ph.L, ph.S, ph.f, ph.p.n_chains,
+                           (ph.p.flags & BDECON_FLAG_AUGMENTED) ? 1LL : 0LL, h->imgs[q].team});
+    }
+    return k;
+}
+
+// Apply a cached plan to a handle whose groups are formed; false if none.
+bool apply_cached_plan(bdecon_handle* h)
+{
+    TuneEntry e;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (!g_tune_cache_on) return false;
+        auto it = g_tune_cache.find(tune_key(h));
+        if (it == g_tune_cache.end()) return false;
+        e = it->second;
+    }
+    h->one_launch = e.one_launch;
+    form_groups(h);
+    if (e.groups.size() != h->groups.size()) {
+        h->one_launch = false;
+        form_groups(h);
+        return false;
+    }
+    for (size_t g = 0; g < h->groups.size(); ++g) {
+        h->groups[g].warps = e.groups[g].warps;
+        h->groups[g].user_warps = true;
+        h->groups[g].streamed = e.groups[g].streamed;
+        h->groups[g].no_stage = !e.groups[g].staged;
+        h->groups[g].user_stage = true;
+    }
+    return true;
+}
+
 bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* ws, size_t ws_bytes, bdecon_handle** out)
 {
     if (!out) return fail(nullptr, BDECON_ERR_INVALID, "out is NULL");
@@ -886,7 +948,14 @@ bdecon_status create_impl(const bdecon_problem* ps, int n, void* stream, void* w
         }
     }
     form_groups(h);
+    // the autotuner's plan for these shapes, if one was tuned in this process
+    const bool cached = apply_cached_plan(h);
     bdecon_status s = make_plan(h);
+    if (s != BDECON_OK && cached) {
+        h->one_launch = false;
+        form_groups(h);
+        s = make_plan(h);
+    }
     if (s != BDECON_OK) return bail(s);
     s = check_device(h);
     if (s != BDECON_OK) return bail(s);
@@ -1626,13 +1695,6 @@ bdecon_status tune_trial(bdecon_handle* h, int len, std::vector<double>& ms)
     return s;
 }
 
-struct TuneChoice {
-    int warps = 0;          // 0: the team's own
-    bool streamed = false;
-    bool staged = false;
-    double ms = 1e300;
-};
-
 }  // namespace
 
 bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* one_launch, double* ms_per_sweep)
@@ -1743,6 +1805,13 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
         s = make_plan(h);
         if (one_launch) *one_launch = h->one_launch ? 1 : 0;
         if (ms_per_sweep) *ms_per_sweep = (h->one_launch ? one.ms : t_groups) / len;
+        if (s == BDECON_OK) {
+            TuneEntry e;
+            e.one_launch = h->one_launch;
+            for (const auto& g : h->groups) e.groups.push_back({g.warps, g.streamed, g.stage == 1, 0.0});
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            if (g_tune_cache_on) g_tune_cache[tune_key(h)] = e;
+        }
     }
     if (s != BDECON_OK) {
         const std::string m = h->err;
@@ -1754,6 +1823,14 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
     }
     cudaFree(snap);
     return s;
+}
+
+bdecon_status bdecon_set_tuning_cache(int32_t enable)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.clear();
+    g_tune_cache_on = enable != 0;
+    return BDECON_OK;
 }
 
 bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int32_t* warps, int32_t* tile_i,

@@ -116,6 +116,46 @@ def test_one_launch_and_autotuned_plans_are_bit_identical(precision):
             np.testing.assert_array_equal(got[p][1], want[p][1])
 
 
+def test_tuning_cache_reuses_the_tuned_plan_and_changes_no_result():
+    # a handle created after an autotune of the same shapes starts with the
+    # tuned plan; with the cache off it starts with the automatic one; the
+    # chains are the same either way
+    probs = _mix()
+    T = 6
+    bdecon.set_tuning_cache(True)
+    auto = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=T + 8)
+    auto_plans = [auto.get_plan(p) for p in range(len(probs))]
+    auto.sweep(T)
+    want = [_collect(auto, p, pr.n_chains) for p, pr in enumerate(probs)]
+    auto.close()
+
+    tuned = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=T + 8)
+    tuned.sweep(1)
+    tuned.set_grouping(True)                 # a shape the automatic plan never takes,
+    tuned.autotune(trial_sweeps=1)           # unless the autotuner keeps it
+    tuned_plans = [tuned.get_plan(p) for p in range(len(probs))]
+    tuned.close()
+
+    again = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=T + 8)
+    assert [again.get_plan(p) for p in range(len(probs))] == tuned_plans
+    again.sweep(T)
+    got = [_collect(again, p, pr.n_chains) for p, pr in enumerate(probs)]
+    again.close()
+    other = bdecon.Sampler(probs[:3], precision=bdecon.BDECON_FP32, max_sweeps=T + 8)   # another key
+    assert [other.get_plan(p) for p in range(3)] == auto_plans[:3]
+    other.close()
+    bdecon.set_tuning_cache(False)
+    off = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=T + 8)
+    assert [off.get_plan(p) for p in range(len(probs))] == auto_plans
+    off.close()
+    bdecon.set_tuning_cache(True)
+    for p, pr in enumerate(probs):
+        for c in range(pr.n_chains):
+            for x, y in zip(got[p][0][c], want[p][0][c]):
+                np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(got[p][1], want[p][1])
+
+
 def test_warps_only_plan_override():
     probs = _mix()
     s = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=8)
