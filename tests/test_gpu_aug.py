@@ -37,16 +37,22 @@ def _aug(**kw):
     return p
 
 
-@pytest.mark.parametrize("kw", [
-    dict(H=20, W=24, L=5, seed=111, refresh_every=4),
-    dict(H=17, W=13, L=3, seed=112, maps=True, refresh_every=0),
-    dict(H=16, W=19, L=5, stride=7, seed=113, maps=True),
-    dict(H=12, W=12, L=7, seed=114, n_chains=2, burn_in=3),
+@pytest.mark.parametrize("kw,plan", [
+    (dict(H=20, W=24, L=5, seed=111, refresh_every=4), None),
+    (dict(H=17, W=13, L=3, seed=112, maps=True, refresh_every=0), None),
+    (dict(H=16, W=19, L=5, stride=7, seed=113, maps=True), None),
+    (dict(H=12, W=12, L=7, seed=114, n_chains=2, burn_in=3), None),
+    # two one-warp update teams per block, several rounds per class step
+    (dict(H=30, W=27, L=5, seed=115, maps=True, refresh_every=4), (3, 3, 2)),
 ])
-def test_fp64_augmented_chain_matches_oracle(kw):
+def test_fp64_augmented_chain_matches_oracle(kw, plan):
     p = _aug(**kw)
     T = 12
     s = bdecon.Sampler(p, precision=bdecon.BDECON_FP64, max_sweeps=T + 4, flags=bdecon.FLAG_ACCEPT_LOG)
+    if plan is not None:
+        s.set_plan(*plan)
+        pl = s.get_plan(0)
+        assert (pl["tile_i"], pl["tile_j"], pl["warps"]) == plan
     s.sweep(T)
     for c in range(p.n_chains):
         ref = O.Oracle(p, chain=c).run(T, want_acc_log=True)

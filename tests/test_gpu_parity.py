@@ -46,8 +46,10 @@ def _run_gpu(prob, T, precision=bdecon.BDECON_FP64, flags=bdecon.FLAG_ACCEPT_LOG
     return out
 
 
-def _compare_exact(prob, T):
-    g = _run_gpu(prob, T)
+def _compare_exact(prob, T, plan=None):
+    g = _run_gpu(prob, T, plan=plan)
+    if plan is not None:
+        assert (g["plan"]["tile_i"], g["plan"]["tile_j"], g["plan"]["warps"]) == tuple(plan)
     sums = []
     for c in range(prob.n_chains):
         ref = O.Oracle(prob, chain=c).run(T, want_acc_log=True)
@@ -86,7 +88,7 @@ def test_fp64_exact_chain_widefield64_50_sweeps():
 def test_plan_invariance(precision):
     prob = synth.small_problem(H=30, W=27, L=5, seed=12, maps=True, n_chains=2, refresh_every=4)
     runs = [_run_gpu(prob, 9, precision=precision, plan=pl)
-            for pl in (None, (2, 3, 1), (3, 3, 4), (1, 2, 2), (4, 5, 8))]
+            for pl in (None, (2, 3, 1), (3, 3, 4), (1, 2, 2), (4, 5, 8), (3, 4, 2), (2, 2, 2))]
     base = runs[0]
     for r in runs[1:]:
         for c in range(prob.n_chains):
@@ -304,6 +306,15 @@ def test_fp64_exact_chain_with_explicit_team(team_warps):
     prob = synth.small_problem(H=22, W=21, L=11, sigma=1.6, seed=71, maps=True, refresh_every=4, burn_in=2)
     prob.team_warps = team_warps
     _compare_exact(prob, 8)
+
+
+@pytest.mark.parametrize("plan", [(3, 3, 2), (2, 4, 2)])
+def test_fp64_exact_chain_two_teams_several_rounds(plan):
+    # blocks of two one-warp update teams over tiles of several patches: after
+    # a class step's first round each team synchronises on its own barrier and
+    # the block meets at the step's end; the chain is still the oracle's
+    prob = synth.small_problem(H=30, W=27, L=5, seed=13, maps=True, n_chains=2, refresh_every=4, burn_in=2)
+    _compare_exact(prob, 10, plan=plan)
 
 
 def test_fp64_exact_chain_with_airy_psf():
