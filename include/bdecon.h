@@ -343,6 +343,18 @@ bdecon_status bdecon_get_plan(bdecon_handle* h, int32_t p, int32_t* blocks, int3
 bdecon_status bdecon_set_staging(bdecon_handle* h, int32_t enable);
 bdecon_status bdecon_get_staging(bdecon_handle* h, int32_t p, int32_t* staged);
 
+/* Lean kernel form (float problems of the marginal sampler on the camera
+ * grid, unstaged plans other than the one-patch one-team form): each update
+ * thread holds half as many window cells in flight (the window of Eq. 6 over
+ * the PSF support, Fig. 5d) and the kernel is built for 64 registers a
+ * thread, so more blocks are resident per SM.  mode -1 (the default): used
+ * for PSF windows of more than 256 pixels (side 17 and up; measured faster
+ * there, slower for smaller windows); 0: never; 1: wherever eligible.
+ * bdecon_autotune tries both.  Results do not change.
+ * bdecon_get_lean reports whether problem p's launch group runs it.        */
+bdecon_status bdecon_set_lean(bdecon_handle* h, int32_t mode);
+bdecon_status bdecon_get_lean(bdecon_handle* h, int32_t p, int32_t* lean);
+
 /* Kernel launches issued by this handle since creation.                    */
 bdecon_status bdecon_launch_count(const bdecon_handle* h, int64_t* launches);
 

@@ -61,7 +61,7 @@ EXPORTS = ["bdecon_workspace_size", "bdecon_create", "bdecon_batch_create", "bde
            "bdecon_server_stop", "bdecon_set_grouping", "bdecon_autotune", "bdecon_set_graph",
            "bdecon_posterior_std", "bdecon_posterior_cv", "bdecon_get_samples", "bdecon_posterior_quantiles",
            "bdecon_get_steps", "bdecon_get_phi", "bdecon_set_staging", "bdecon_get_staging",
-           "bdecon_set_tuning_cache"]
+           "bdecon_set_tuning_cache", "bdecon_set_lean", "bdecon_get_lean"]
 
 JOB_QUEUED, JOB_RUNNING, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True):
         "bdecon_get_plan": [H, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)],
         "bdecon_set_staging": [H, i32],
         "bdecon_get_staging": [H, i32, C.POINTER(i32)],
+        "bdecon_set_lean": [H, i32],
+        "bdecon_get_lean": [H, i32, C.POINTER(i32)],
         "bdecon_launch_count": [H, C.POINTER(i64)],
         "bdecon_set_timing": [H, i32],
         "bdecon_sweep_kernel_time": [H, dp, C.POINTER(i64)],
@@ -415,6 +417,16 @@ class Sampler:
 
     def set_staging(self, enable: bool = True):
         self._ck(self.L.bdecon_set_staging(self.h, int(bool(enable))))
+
+    def set_lean(self, mode: int = -1):
+        """Lean kernel form: -1 automatic (default), 0 never, 1 wherever eligible."""
+        self._ck(self.L.bdecon_set_lean(self.h, int(mode)))
+
+    def lean(self, p: int = 0) -> int:
+        """1 when problem p's launch group runs the lean kernel form, else 0."""
+        v = C.c_int32()
+        self._ck(self.L.bdecon_get_lean(self.h, p, C.byref(v)))
+        return int(v.value)
 
     def staged(self, p: int = 0) -> int:
         """1 when problem p's launch group runs with window staging, else 0."""

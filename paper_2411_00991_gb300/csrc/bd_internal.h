@@ -89,6 +89,13 @@ struct Chain {
                                      // (mu, cumulants c1..c4, c5..c6) for window staging, or null
 };
 
+// Window pixels per thread fetched in one batch by the sweep kernel, and by
+// its lean form (which has a 64-register budget: 4 resident 256-thread
+// blocks per SM instead of 3)
+constexpr int kMaxPx = 4;
+constexpr int kLeanPx = 2;
+constexpr int kLeanMinCells = 256;   // the lean form by default for PSF windows larger than this
+
 struct SweepArgs {
     const Image* imgs;
     const Chain* chains;
@@ -106,6 +113,8 @@ struct SweepArgs {
     int stage;                       // 1: window staging -- each update's expected-image and cumulant window
                                      // (and, streamed, its patch spectrum) copied to shared memory by the TMA
                                      // engine, the next round's while the current one computes; 0: none
+    int lean;                        // 1: the lean float form (fewer window cells in flight per thread, a
+                                     // 64-register budget, more resident warps); same results
 };
 
 // Window staging (float marginal sampler on the camera grid).  The window of
@@ -248,7 +257,7 @@ void launch_sample_phi(const Image& im, const Chain& ch, int t, int* err, cudaSt
 template <typename T>
 cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem, cudaStream_t st);
 template <typename T>
-int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine, int stg);
+int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine, int stg, bool solo, bool lean);
 // zero every chain's progress words and trace partials
 void launch_reset(const Image* d_imgs, const Chain* d_chains, int n_chains, int n_slots, cudaStream_t st,
                   int64_t* launches);

@@ -34,6 +34,7 @@
 #include <type_traits>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 
 #include "bd_device.cuh"
@@ -105,7 +106,6 @@ __device__ __forceinline__ void twiddle(const T* tw, const Shape& sh, int kl, in
     wi = eh[0] * ew[1] + eh[1] * ew[0];
 }
 
-constexpr int kMaxPx = 4;   // window pixels per thread fetched in one batch
 
 // Window cell k (0 <= k < Lc^2) of object pixel (i, j): the camera pixel
 // (aa, bb) it weighs on and the entry kw of the effective kernel Ke (Le x Le)
@@ -157,10 +157,10 @@ __device__ __forceinline__ void proposal(const Image& im, const Chain& ch, int m
 // and bad flag in out[0..1].  muv keeps the fetched expected image values.
 // Fetch the first batch of a thread's window values (expected image and
 // cached cumulants) so the loads are in flight while other work proceeds.
-template <typename T, bool CUM, bool FINE>
+template <typename T, bool CUM, bool FINE, int NPX = kMaxPx>
 __device__ __forceinline__ void window_fetch(const T* mu_g, const float4* cum_g, const float2* cum2_g,
-                                             const Image& im, int i, int j, int lt, T (&muv)[kMaxPx],
-                                             float4 (&cq)[kMaxPx], float2 (&cq2)[kMaxPx], int k0)
+                                             const Image& im, int i, int j, int lt, T (&muv)[NPX],
+                                             float4 (&cq)[NPX], float2 (&cq2)[NPX], int k0)
 {
     const int NT = im.team;
     // camera grid: the cell's row and column (k / L, k mod L) are advanced
@@ -169,7 +169,7 @@ __device__ __forceinline__ void window_fetch(const T* mu_g, const float4* cum_g,
     int kr = FINE ? 0 : k0 / L, kc = FINE ? 0 : k0 - kr * L;
     const int dr = FINE ? 0 : NT / L, dc = FINE ? 0 : NT - dr * L;
 #pragma unroll
-    for (int jj = 0; jj < kMaxPx; ++jj) {
+    for (int jj = 0; jj < NPX; ++jj) {
         const int k = k0 + jj * NT;
         int aa, bb, kw;
         bool in;
@@ -194,20 +194,20 @@ __device__ __forceinline__ void window_fetch(const T* mu_g, const float4* cum_g,
     }
 }
 
-template <typename T, bool RES, bool CUM, bool FINE>
+template <typename T, bool RES, bool CUM, bool FINE, int NPX = kMaxPx>
 __device__ __forceinline__ void lik_partial(const T* mu_g, const float4* cum_g, const float2* cum2_g, const Dat4<T>* dat_s,
                                             const Dat4<T>* dat_g, const T* Ks, const Image& im, int i, int j,
-                                            int a_lo, int b_lo, int rw, int lt, int NT, T delta, T (&muv)[kMaxPx],
-                                            T* out, int lane, float4 (&cq)[kMaxPx], float2 (&cq2)[kMaxPx],
+                                            int a_lo, int b_lo, int rw, int lt, int NT, T delta, T (&muv)[NPX],
+                                            T* out, int lane, float4 (&cq)[NPX], float2 (&cq2)[NPX],
                                             bool prefetched)
 {
     const int W = im.W, LL = FINE ? im.Lc * im.Lc : im.L * im.L;
     T accL = 0;
     bool badL = false;
-    for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
-        if (!(prefetched && k0 == lt)) window_fetch<T, CUM, FINE>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, k0);
+    for (int k0 = lt; k0 < LL; k0 += NT * NPX) {
+        if (!(prefetched && k0 == lt)) window_fetch<T, CUM, FINE, NPX>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, k0);
 #pragma unroll
-        for (int jj = 0; jj < kMaxPx; ++jj) {
+        for (int jj = 0; jj < NPX; ++jj) {
             const int k = k0 + jj * NT;
             // on the camera grid the fetched window tells the cells apart (mu > 0
             // inside, -1 outside), so the geometry is needed only to read the
@@ -293,13 +293,13 @@ __device__ __forceinline__ void lik_partial_staged(const float* wmu, const float
 }
 
 // Augmented sampler: the window's expected image and photon counts.
-template <typename T, bool FINE>
+template <typename T, bool FINE, int NPX = kMaxPx>
 __device__ __forceinline__ void window_fetch_aug(const T* mu_g, const T* phi_g, const Image& im, int i, int j,
-                                                 T (&muv)[kMaxPx], T (&phv)[kMaxPx], int k0)
+                                                 T (&muv)[NPX], T (&phv)[NPX], int k0)
 {
     const int NT = im.team;
 #pragma unroll
-    for (int jj = 0; jj < kMaxPx; ++jj) {
+    for (int jj = 0; jj < NPX; ++jj) {
         const int k = k0 + jj * NT;
         int aa, bb, kw;
         const bool in = win_cell<FINE>(im, i, j, k, aa, bb, kw);
@@ -313,18 +313,18 @@ __device__ __forceinline__ void window_fetch_aug(const T* mu_g, const T* phi_g, 
 //   sum_n phi_n log(1 + delta K/mu_n) - delta K,
 // a proposal making some mu'_n <= 0 being impossible.  Same thread
 // assignment and reduction as lik_partial.
-template <typename T, bool FINE>
+template <typename T, bool FINE, int NPX = kMaxPx>
 __device__ __forceinline__ void lik_partial_aug(const T* mu_g, const T* phi_g, const T* Ks, const Image& im, int i,
-                                                int j, int lt, int NT, T delta, T (&muv)[kMaxPx], T (&phv)[kMaxPx],
+                                                int j, int lt, int NT, T delta, T (&muv)[NPX], T (&phv)[NPX],
                                                 T* out, int lane, bool prefetched)
 {
     const int LL = FINE ? im.Lc * im.Lc : im.L * im.L;
     T accL = 0;
     bool badL = false;
-    for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
-        if (!(prefetched && k0 == lt)) window_fetch_aug<T, FINE>(mu_g, phi_g, im, i, j, muv, phv, k0);
+    for (int k0 = lt; k0 < LL; k0 += NT * NPX) {
+        if (!(prefetched && k0 == lt)) window_fetch_aug<T, FINE, NPX>(mu_g, phi_g, im, i, j, muv, phv, k0);
 #pragma unroll
-        for (int jj = 0; jj < kMaxPx; ++jj) {
+        for (int jj = 0; jj < NPX; ++jj) {
             const int k = k0 + jj * NT;
             int aa = 0, bb = 0, kw = k;
             const bool in = FINE ? win_cell<FINE>(im, i, j, k, aa, bb, kw) : muv[jj] != (T)-1;
@@ -357,10 +357,16 @@ __device__ __forceinline__ void lik_partial_aug(const T* mu_g, const T* phi_g, c
 // streamed plans, its patch spectrum -- is copied into a shared-memory buffer
 // of its team by the TMA engine, the next round's copy in flight while the
 // current round computes (two buffers per team)
-template <typename T, bool RES, bool AUG, bool FINE, bool SOLO = false, int STG = 0>
-__global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_sweep(SweepArgs a)
+// LEAN: the float marginal camera-grid form (unstaged, not the one-team
+// form) with half the window batch held in registers and a 64-register
+// budget, for more resident warps per SM; the per-thread cell order, and so
+// every result, is that of the other forms
+template <typename T, bool RES, bool AUG, bool FINE, bool SOLO = false, int STG = 0, bool LEAN = false>
+__global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4 : 3) : 2) k_sweep(SweepArgs a)
 {
     using P = Prec<T>;
+    static_assert(!LEAN || (std::is_same<T, float>::value && !AUG && !FINE && !SOLO && STG == 0), "lean: float marginal camera grid");
+    constexpr int NPX = LEAN ? kLeanPx : kMaxPx;
     // float sweeps of the marginal sampler use the cumulant cache; the
     // augmented sampler (AUG) scores windows from the photon counts instead
     constexpr bool CUM = std::is_same<T, float>::value && !AUG;
@@ -732,10 +738,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             T z = 0, lu = 0, r_old = 0, r_new = 0, delta = 0;
             bool badP = false;
             T* spec_p = RES ? spec_s + (size_t)q * 2 * im.max_nhalf : spec_g + 2 * im.patch_off[pi * im.npj + pj];
-            T muv[kMaxPx];
-            float4 cq[AUG ? 1 : kMaxPx];
-            float2 cq2[AUG ? 1 : kMaxPx];
-            T phv[AUG ? kMaxPx : 1];
+            T muv[NPX];
+            float4 cq[AUG ? 1 : NPX];
+            float2 cq2[AUG ? 1 : NPX];
+            T phv[AUG ? NPX : 1];
             // staged window of this round (STG): buffer e & 1 of the team
             const int e_cur = cs * rounds + r, sb = e_cur & 1;
             const float* wmu = reinterpret_cast<const float*>(stg_buf(sb) + stp.mu);
@@ -753,8 +759,8 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // the window's first batch is fetched before the prior work so its
             // latency overlaps the arithmetic below
             if (active && !SWIN) {
-                if constexpr (AUG) window_fetch_aug<T, FINE>(mu_g, phi_g, im, i, j, muv, phv, lt);
-                else window_fetch<T, CUM, FINE>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, lt);
+                if constexpr (AUG) window_fetch_aug<T, FINE, NPX>(mu_g, phi_g, im, i, j, muv, phv, lt);
+                else window_fetch<T, CUM, FINE, NPX>(mu_g, cum_g, cum2_g, im, i, j, lt, muv, cq, cq2, lt);
             }
             // a2 + a4: proposal and prior change (own tile state only)
             if (active) {
@@ -794,13 +800,13 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             // accepted an update since this block last waited for it.
             if (active) {
                 if constexpr (AUG)
-                    lik_partial_aug<T, FINE>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane,
+                    lik_partial_aug<T, FINE, NPX>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane,
                                              true);
                 else if constexpr (SWIN)
                     lik_partial_staged<RES>(wmu, wcum, wcum2, BW, wdx, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt,
                                             NT, delta, red2 + twarp * 4, lane);
                 else
-                    lik_partial<T, RES, CUM, FINE>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
+                    lik_partial<T, RES, CUM, FINE, NPX>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
                                              delta, muv, red2 + twarp * 4, lane, cq, cq2, true);
             }
             // a5: Metropolis-Hastings decision with the Hastings term of the log-space
@@ -888,7 +894,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             if (stale) {
                 if (active) {
                     if constexpr (AUG) {
-                        lik_partial_aug<T, FINE>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4,
+                        lik_partial_aug<T, FINE, NPX>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4,
                                                  lane, false);
                     } else if constexpr (SWIN) {
                         // the speculative copy is stale: copy the window again (every
@@ -898,7 +904,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
                         lik_partial_staged<RES>(wmu, wcum, wcum2, BW, wdx, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw,
                                                 lt, NT, delta, red2 + twarp * 4, lane);
                     } else {
-                        lik_partial<T, RES, CUM, FINE>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
+                        lik_partial<T, RES, CUM, FINE, NPX>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
                                                  delta, muv, red2 + twarp * 4, lane, cq, cq2, false);
                     }
                 }
@@ -914,10 +920,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
             if (active && nonfin && lt == 0) report_nonfinite(a.err, ch.chain, m, t, (double)dL, (double)dP);
             if (active) {
                 if (accept) {
-                    const bool one_batch = LL <= NT * kMaxPx;
-                    for (int k0 = lt; k0 < LL; k0 += NT * kMaxPx) {
+                    const bool one_batch = LL <= NT * NPX;
+                    for (int k0 = lt; k0 < LL; k0 += NT * NPX) {
 #pragma unroll
-                        for (int jj = 0; jj < kMaxPx; ++jj) {
+                        for (int jj = 0; jj < NPX; ++jj) {
                             const int k = k0 + jj * NT;
                             int aa, bb, kw;
                             if (win_cell<FINE>(im, i, j, k, aa, bb, kw)) {
@@ -1054,9 +1060,12 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? 3 : 2) k_
 // The sweep kernel's form: tile state resident in shared memory or not,
 // augmented sampler or not, object lattice finer than the camera or not.
 template <typename T>
-const void* sweep_fn(bool res, bool aug, bool fine, bool solo, int stg)
+const void* sweep_fn(bool res, bool aug, bool fine, bool solo, int stg, bool lean = false)
 {
     if constexpr (std::is_same<T, float>::value) {
+        if (lean && !aug && !fine && !solo && stg == 0)
+            return res ? (const void*)k_sweep<T, true, false, false, false, 0, true>
+                       : (const void*)k_sweep<T, false, false, false, false, 0, true>;
         if (solo && res && !fine)
             return aug ? (const void*)k_sweep<T, true, true, false, true> : (const void*)k_sweep<T, true, false, false, true>;
         if (stg == 1 && !aug && !fine && !solo)
@@ -1071,20 +1080,20 @@ const void* sweep_fn(bool res, bool aug, bool fine, bool solo, int stg)
     return res ? (const void*)k_sweep<T, true, false, false> : (const void*)k_sweep<T, false, false, false>;
 }
 
-// Raise a kernel form's dynamic shared-memory limit to at least smem (the
-// limit only grows, so launches with smaller plans stay valid).
+// Raise a kernel form's dynamic shared-memory limit to at least smem.  The
+// limit is kept per kernel function (several form flags can name the same
+// function), and it only grows, so launches with smaller plans stay valid.
 template <typename T>
-cudaError_t ensure_smem_limit(bool res, bool aug, bool fine, bool solo, int stg, size_t smem)
+cudaError_t ensure_smem_limit(bool res, bool aug, bool fine, bool solo, int stg, size_t smem, bool lean = false)
 {
-    static std::atomic<size_t> limit[64];
+    static std::map<const void*, size_t> limit;
     static std::mutex mu;
-    const int form = (res ? 1 : 0) | (aug ? 2 : 0) | (fine ? 4 : 0) | (solo ? 8 : 0) | (stg << 4);
-    if (limit[form].load() >= smem) return cudaSuccess;
+    const void* fn = sweep_fn<T>(res, aug, fine, solo, stg, lean);
     std::lock_guard<std::mutex> lock(mu);
-    if (limit[form].load() >= smem) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(sweep_fn<T>(res, aug, fine, solo, stg), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e == cudaSuccess) limit[form].store(smem);
+    size_t& cur = limit[fn];
+    if (cur >= smem) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cur = smem;
     return e;
 }
 
@@ -1096,8 +1105,8 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
 {
     SweepArgs args = a;
     void* kargs[] = {&args};
-    const void* fn = sweep_fn<T>(a.resident, a.aug, a.fine, a.solo, a.stage);
-    cudaError_t e = ensure_smem_limit<T>(a.resident, a.aug, a.fine, a.solo, a.stage, smem);
+    const void* fn = sweep_fn<T>(a.resident, a.aug, a.fine, a.solo, a.stage, a.lean);
+    cudaError_t e = ensure_smem_limit<T>(a.resident, a.aug, a.fine, a.solo, a.stage, smem, a.lean);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1113,23 +1122,24 @@ cudaError_t launch_sweep(const SweepArgs& a, int grid, int threads, size_t smem,
 }
 
 // Blocks of the sweep kernel resident per SM for this block size and shared
-// memory: the smallest over its resident and streamed forms (and the one-team
-// form) so that either fits, or over the staged forms of a staging plan.
+// memory: the smallest over the forms a plan of this kind may launch -- for a
+// one-team plan (solo) its one-team form, else the resident and streamed
+// forms (so that either fits), or the staged forms of a staging plan.
 template <typename T>
-int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine, int stg)
+int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine, int stg, bool solo, bool lean)
 {
     int best = 1 << 30;
-    for (int form = 0; form < 4; ++form) {   // resident or not, x one-team form or not
-        const bool res = (form & 1) != 0, solo = (form & 2) != 0 && stg == 0;
-        const int st = stg;
-        if (st != 0 && (solo || (form & 2) != 0)) continue;
+    for (int res = 0; res <= 1; ++res) {
+        const bool so = solo && stg == 0;
+        if (so && res == 0) continue;   // the one-team form is resident
         int n = 0;
-        if (ensure_smem_limit<T>(res, aug, fine, solo, st, smem) != cudaSuccess) {
+        const bool ln = lean && !so;
+        if (ensure_smem_limit<T>(res != 0, aug, fine, so, stg, smem, ln) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_fn<T>(res, aug, fine, solo, st), threads, smem) !=
-            cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, sweep_fn<T>(res != 0, aug, fine, so, stg, ln), threads,
+                                                          smem) != cudaSuccess)
             return 0;
         best = n < best ? n : best;
     }
@@ -1138,8 +1148,8 @@ int sweep_blocks_per_sm(int threads, size_t smem, bool aug, bool fine, int stg)
 
 template cudaError_t launch_sweep<float>(const SweepArgs&, int, int, size_t, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs&, int, int, size_t, cudaStream_t);
-template int sweep_blocks_per_sm<float>(int, size_t, bool, bool, int);
-template int sweep_blocks_per_sm<double>(int, size_t, bool, bool, int);
+template int sweep_blocks_per_sm<float>(int, size_t, bool, bool, int, bool, bool);
+template int sweep_blocks_per_sm<double>(int, size_t, bool, bool, int, bool, bool);
 
 // ---------------------------------------------------------------- delta --
 // The same per-update arithmetic for one hypothetical proposal (testing):

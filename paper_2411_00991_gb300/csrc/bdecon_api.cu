@@ -75,6 +75,9 @@ struct Group {
     bool no_stage = true;              // window staging not allowed in this group's plan
     bool many = false;                 // every problem has many updates per class step: two teams per block
     bool user_stage = false;           // no_stage set by the autotuner, not by the handle's setting
+    int lean_mode = -1;                // lean kernel form: -1 automatic, 0 off, 1 on where eligible
+    int user_lean = -2;                // lean_mode set by the autotuner (-2: not set; the handle's setting)
+    bool lean = false;                 // the plan runs the lean form
     int chain_off = 0, n_chains = 0;   // slice of the group-ordered chain table
 };
 
@@ -96,6 +99,7 @@ struct bdecon_handle {
     std::vector<Group> groups;
     bool one_launch = false;            // all problems in one launch instead of one per (L, S, team)
     int staging = 0;                    // window staging by the TMA engine in eligible groups (1) or not (0)
+    int lean = -1;                      // lean kernel form: -1 automatic, 0 off, 1 on where eligible
     std::vector<int> prob_group;        // problem -> group
     std::vector<Chain> gch;             // host copy of the group-ordered chain table
     size_t o_gchains = 0;
@@ -279,20 +283,21 @@ void describe(ProbHost& ph)
 // Blocks per SM of the sweep kernel's forms for this launch shape, memoized:
 // the planner asks at every tile-growth step, and the answer depends only on
 // the device, the precision, the block size, the shared memory and the form.
-int occupancy(int prec, int threads, size_t smem, bool aug, bool fine, int stg)
+int occupancy(int prec, int threads, size_t smem, bool aug, bool fine, int stg, bool solo = false, bool lean = false)
 {
     static std::mutex mu;
     static std::map<std::vector<long long>, int> memo;
     int dev = 0;
     cudaGetDevice(&dev);
-    const std::vector<long long> key = {dev, prec, threads, (long long)smem, aug ? 1 : 0, fine ? 1 : 0, stg};
+    const std::vector<long long> key = {dev, prec, threads, (long long)smem, aug ? 1 : 0, fine ? 1 : 0, stg, solo ? 1 : 0,
+                                        lean ? 1 : 0};
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = memo.find(key);
         if (it != memo.end()) return it->second;
     }
-    const int n = prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug, fine, stg)
-                                      : sweep_blocks_per_sm<double>(threads, smem, aug, fine, stg);
+    const int n = prec == BDECON_FP32 ? sweep_blocks_per_sm<float>(threads, smem, aug, fine, stg, solo, lean)
+                                      : sweep_blocks_per_sm<double>(threads, smem, aug, fine, stg, solo, lean);
     if (n > 0) {
         std::lock_guard<std::mutex> lock(mu);
         memo[key] = n;
@@ -376,6 +381,13 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
     // form instead (its windows are read once per step from L2 by many blocks
     // at once, and it needs no buffers)
     bool stage_ok = precision == BDECON_FP32 && !g.aug && !g.fine && !g.no_stage;
+    // lean form (unstaged float marginal camera-grid plans): automatically
+    // for windows of more than kLeanMinCells cells (measured on the 64-frame
+    // batch: faster from PSF side 17 up, slower at 9 and 13, where its extra
+    // window batches cost more than its extra resident warps give)
+    bool want_lean = precision == BDECON_FP32 && !g.aug && !g.fine && g.lean_mode != 0;
+    if (want_lean && g.lean_mode < 0)
+        for (const PlanItem* it : items) want_lean = want_lean && it->ph->L * it->ph->L > kLeanMinCells;
     for (const PlanItem* it : items) stage_ok = stage_ok && it->ph->stage_ok;
     bool done = false;
     for (int attempt = stage_ok ? 0 : 1; attempt < 2 && !done; ++attempt) {
@@ -388,7 +400,8 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
                 int tot = 0;
                 for (const PlanItem* it : items) tot += item_blocks(*it);
                 if (smem <= kMaxSmem) {
-                    const int bps = occupancy(precision, g.threads, smem, g.aug, g.fine, stage);
+                    const int bps = occupancy(precision, g.threads, smem, g.aug, g.fine, stage, false,
+                                              want_lean && stage == 0);
                     if (bps > 0 && tot <= bps * sms) {
                         g.smem = smem;
                         g.resident = resident;
@@ -415,7 +428,7 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
                 const size_t smem = items_smem(items, 1, ts, g.threads, 0);
                 int tot = 0;
                 for (const PlanItem* it : items) tot += item_blocks(*it);
-                const int bps = smem <= kMaxSmem ? occupancy(precision, g.threads, smem, g.aug, g.fine, 0) : 0;
+                const int bps = smem <= kMaxSmem ? occupancy(precision, g.threads, smem, g.aug, g.fine, 0, true) : 0;
                 if (bps > 0 && tot <= bps * sms) {
                     g.smem = smem;
                     g.resident = 1;
@@ -439,6 +452,15 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
     }
     g.solo = g.stage == 0;
     for (const PlanItem* it : items) g.solo = g.solo && it->tpi == 1 && it->tpj == 1 && g.threads == it->team;
+    if (g.solo) {
+        // a one-patch one-team plan found above was sized for the other forms:
+        // it runs the one-team form only if that form's blocks are co-resident too
+        int tot = 0;
+        for (const PlanItem* it : items) tot += item_blocks(*it);
+        const int bps = occupancy(precision, g.threads, g.smem, g.aug, g.fine, 0, true);
+        if (!(bps > 0 && tot <= bps * sms)) g.solo = false;
+    }
+    g.lean = want_lean && g.stage == 0 && !g.solo;
     int base = 0;
     for (PlanItem* it : items) {
         const int nti = (it->ph->npi + it->tpi - 1) / it->tpi, ntj = (it->ph->npj + it->tpj - 1) / it->tpj;
@@ -465,6 +487,7 @@ bdecon_status make_plan(bdecon_handle* h)
     drop_graphs(h);   // captured launches carry the old grid and tables
     for (auto& g : h->groups) {
         if (!g.user_stage) g.no_stage = h->staging == 0;
+        g.lean_mode = g.user_lean != -2 ? g.user_lean : h->lean;
         std::vector<PlanItem> items(g.probs.size());
         std::vector<PlanItem*> ptrs;
         for (size_t k = 0; k < g.probs.size(); ++k) {
@@ -687,6 +710,7 @@ struct TuneChoice {
     bool streamed = false;
     bool staged = false;
     double ms = 1e300;
+    bool lean = false;
 };
 
 // Tuning cache: the autotuner's choices, kept for the life of the process
@@ -707,7 +731,7 @@ std::vector<long long> tune_key(const bdecon_handle* h)
 {
     int dev = 0;
     cudaGetDevice(&dev);
-    std::vector<long long> k = {dev, h->sms, h->precision, h->staging};
+    std::vector<long long> k = {dev, h->sms, h->precision, h->staging, h->lean};
     for (size_t q = 0; q < h->probs.size(); ++q) {
         const ProbHost& ph = h->probs[q];
         k.insert(k.end(), {ph.H, ph.W, ph.L, ph.S, ph.f, ph.p.n_chains,
@@ -740,6 +764,7 @@ bool apply_cached_plan(bdecon_handle* h)
         h->groups[g].streamed = e.groups[g].streamed;
         h->groups[g].no_stage = !e.groups[g].staged;
         h->groups[g].user_stage = true;
+        h->groups[g].user_lean = e.groups[g].lean ? 1 : 0;
     }
     return true;
 }
@@ -1067,6 +1092,7 @@ bdecon_status run_segment(LaunchSet& ls, int len, cudaStream_t st, bdecon_handle
         a.fine = g.fine ? 1 : 0;
         a.solo = g.solo ? 1 : 0;
         a.stage = g.stage;
+        a.lean = g.lean ? 1 : 0;
         cudaError_t e = eh->precision == BDECON_FP32 ? launch_sweep<float>(a, g.grid, g.threads, g.smem, st)
                                                      : launch_sweep<double>(a, g.grid, g.threads, g.smem, st);
         if (e != cudaSuccess)
@@ -1671,6 +1697,35 @@ bdecon_status bdecon_get_staging(bdecon_handle* h, int32_t p, int32_t* staged)
     return BDECON_OK;
 }
 
+bdecon_status bdecon_set_lean(bdecon_handle* h, int32_t mode)
+{
+    if (!h) return fail(nullptr, BDECON_ERR_INVALID, "handle is NULL");
+    if (mode < -1 || mode > 1) return fail(h, BDECON_ERR_INVALID, "lean mode %d (-1, 0 or 1)", mode);
+    bdecon_status s = check_device(h);
+    if (s != BDECON_OK) return s;
+    const int old = h->lean;
+    const std::vector<Group> old_groups = h->groups;
+    h->lean = mode;
+    for (auto& g : h->groups) g.user_lean = -2;
+    s = make_plan(h);
+    if (s != BDECON_OK) {
+        const std::string m = h->err;
+        h->lean = old;
+        h->groups = old_groups;
+        make_plan(h);
+        h->err = m;
+    }
+    return s;
+}
+
+bdecon_status bdecon_get_lean(bdecon_handle* h, int32_t p, int32_t* lean)
+{
+    if (!h || !lean) return fail(h, BDECON_ERR_INVALID, "bad arguments");
+    if (p < 0 || p >= (int)h->probs.size()) return fail(h, BDECON_ERR_INVALID, "problem index %d", p);
+    *lean = h->groups[h->prob_group[p]].lean ? 1 : 0;
+    return BDECON_OK;
+}
+
 namespace {
 
 // One autotuner trial: a segment of len sweeps in the current plan, timed
@@ -1735,27 +1790,37 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
     for (const auto& ph : h->probs) any_stage = any_stage || ph.stage_ok;
     // (staged shapes are tried with the team's own warps only: their buffers
     // already limit the blocks per SM)
+    // (the lean form is tried where it applies: float, unstaged)
+    const int n_lean = h->precision == BDECON_FP32 ? 2 : 1;
     for (int st = 0; st <= (any_stage ? 1 : 0) && s == BDECON_OK; ++st)
-        for (int streamed = 0; streamed <= 1 && s == BDECON_OK; ++streamed)
-            for (int mi = 0; mi < (st ? 1 : 3) && s == BDECON_OK; ++mi) {
-                bool any = false;
-                for (auto& g : h->groups) {
-                    const int tw = g.team / 32, w = std::min(8, tw * kMult[mi]);
-                    any = any || (mi == 0 || w != std::min(8, tw * kMult[mi - 1]));
-                    g.warps = w;
-                    g.user_warps = true;
-                    g.streamed = streamed != 0;
-                    g.no_stage = st == 0;
-                    g.user_stage = true;
+        for (int ln = 0; ln < (st ? 1 : n_lean) && s == BDECON_OK; ++ln)
+            for (int streamed = 0; streamed <= 1 && s == BDECON_OK; ++streamed)
+                for (int mi = 0; mi < (st ? 1 : 3) && s == BDECON_OK; ++mi) {
+                    bool any = false;
+                    for (auto& g : h->groups) {
+                        const int tw = g.team / 32, w = std::min(8, tw * kMult[mi]);
+                        any = any || (mi == 0 || w != std::min(8, tw * kMult[mi - 1]));
+                        g.warps = w;
+                        g.user_warps = true;
+                        g.streamed = streamed != 0;
+                        g.no_stage = st == 0;
+                        g.user_stage = true;
+                        g.user_lean = ln;
+                    }
+                    if (!any) continue;
+                    if (make_plan(h) != BDECON_OK) continue;   // no co-resident plan of this shape
+                    if (ln == 1) {   // a lean trial only where some group runs the lean form
+                        bool some = false;
+                        for (const auto& g : h->groups) some = some || g.lean;
+                        if (!some) continue;
+                    }
+                    std::vector<double> ms;
+                    s = tune_trial(h, len, ms);
+                    if (s == BDECON_OK) s = restore();
+                    for (size_t g = 0; g < ms.size() && s == BDECON_OK; ++g)
+                        if (ms[g] < best[g].ms)
+                            best[g] = {h->groups[g].warps, streamed != 0, h->groups[g].stage == 1, ms[g], h->groups[g].lean};
                 }
-                if (!any) continue;
-                if (make_plan(h) != BDECON_OK) continue;   // no co-resident plan of this shape
-                std::vector<double> ms;
-                s = tune_trial(h, len, ms);
-                if (s == BDECON_OK) s = restore();
-                for (size_t g = 0; g < ms.size() && s == BDECON_OK; ++g)
-                    if (ms[g] < best[g].ms) best[g] = {h->groups[g].warps, streamed != 0, h->groups[g].stage == 1, ms[g]};
-            }
     double t_groups = 0;
     for (const auto& b : best) t_groups += b.ms;
     // (b) one launch over every problem
@@ -1779,7 +1844,7 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
                     std::vector<double> ms;
                     s = tune_trial(h, len, ms);
                     if (s == BDECON_OK) s = restore();
-                    if (s == BDECON_OK && ms[0] < one.ms) one = {w, streamed != 0, g.stage == 1, ms[0]};
+                    if (s == BDECON_OK && ms[0] < one.ms) one = {w, streamed != 0, g.stage == 1, ms[0], g.lean};
                     behind = s == BDECON_OK && one.ms > 1.5 * t_groups;
                 }
     }
@@ -1793,6 +1858,7 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
             h->groups[0].streamed = one.streamed;
             h->groups[0].no_stage = !one.staged;
             h->groups[0].user_stage = true;
+            h->groups[0].user_lean = one.lean ? 1 : 0;
         } else {
             for (size_t g = 0; g < h->groups.size(); ++g) {
                 h->groups[g].warps = best[g].warps;
@@ -1800,6 +1866,7 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
                 h->groups[g].streamed = best[g].streamed;
                 h->groups[g].no_stage = !best[g].staged;
                 h->groups[g].user_stage = true;
+                h->groups[g].user_lean = best[g].lean ? 1 : 0;
             }
         }
         s = make_plan(h);
@@ -1808,7 +1875,7 @@ bdecon_status bdecon_autotune(bdecon_handle* h, int32_t trial_sweeps, int32_t* o
         if (s == BDECON_OK) {
             TuneEntry e;
             e.one_launch = h->one_launch;
-            for (const auto& g : h->groups) e.groups.push_back({g.warps, g.streamed, g.stage == 1, 0.0});
+            for (const auto& g : h->groups) e.groups.push_back({g.warps, g.streamed, g.stage == 1, 0.0, g.lean});
             std::lock_guard<std::mutex> lock(g_tune_mu);
             if (g_tune_cache_on) g_tune_cache[tune_key(h)] = e;
         }

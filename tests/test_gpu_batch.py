@@ -156,6 +156,45 @@ def test_tuning_cache_reuses_the_tuned_plan_and_changes_no_result():
         np.testing.assert_array_equal(got[p][1], want[p][1])
 
 
+def test_lean_form_is_bit_identical():
+    # the lean kernel form holds fewer window cells in flight per thread and
+    # has a smaller register budget; the cells, their order and the reductions
+    # are those of the default form, so chains are bit-identical -- with the
+    # form forced on, off, and switched between sweeps, on multi-patch tiles
+    # (one- and two-team blocks, several rounds per class step)
+    probs = _mix()
+    T = 9
+
+    def run(modes):
+        s = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=T + 4)
+        for p in range(len(probs)):
+            s.set_plan(2, 3, 2 if p % 2 else 0, p=p)
+        done = 0
+        for mode, n in modes:
+            s.set_lean(mode)
+            lean = [s.lean(p) for p in range(len(probs))]
+            assert all(lean) if mode == 1 else not any(lean)
+            s.sweep(n)
+            done += n
+        assert done == T
+        out = [_collect(s, p, pr.n_chains) for p, pr in enumerate(probs)]
+        s.close()
+        return out
+
+    want = run([(0, T)])
+    for got in (run([(1, T)]), run([(1, 4), (0, T - 4)])):
+        for p, pr in enumerate(probs):
+            for c in range(pr.n_chains):
+                for x, y in zip(got[p][0][c], want[p][0][c]):
+                    np.testing.assert_array_equal(x, y)
+            np.testing.assert_array_equal(got[p][1], want[p][1])
+    d = bdecon.Sampler(probs, precision=bdecon.BDECON_FP64, max_sweeps=4)
+    d.set_plan(2, 3, 0, p=0)
+    d.set_lean(1)
+    assert not any(d.lean(p) for p in range(len(probs)))   # a float form only
+    d.close()
+
+
 def test_warps_only_plan_override():
     probs = _mix()
     s = bdecon.Sampler(probs, precision=bdecon.BDECON_FP32, max_sweeps=8)
