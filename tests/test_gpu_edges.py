@@ -81,3 +81,32 @@ def test_degenerate_frames_exact_chain(kw, T):
     np.testing.assert_allclose(s.posterior_mean(), ref["mean"], rtol=RTOL)
     assert math.isfinite(s.log_posterior())
     s.close()
+
+
+def test_one_patch_plan_without_room_for_the_one_team_form():
+    # the 512x512 frame with a 4-warp update team: one patch per block fits
+    # the general kernel forms (lean: 8 blocks of 128 threads per SM) but not
+    # the one-team form (80 registers: 6 per SM, fewer than 1024 blocks), so
+    # the plan keeps one patch per block in the general form; every block is
+    # co-resident, and the chain equals that of a plan of 2 x 2-patch tiles
+    p = synth.widefield_512()
+    p.truth = None
+    p.team_warps = 4
+    T = 3
+    out = []
+    for plan in (None, (2, 2, 0)):
+        s = bdecon.Sampler(p, precision=bdecon.BDECON_FP32, max_sweeps=T + 4)
+        if plan is not None:
+            s.set_plan(*plan)
+        pl = s.get_plan(0)
+        if plan is None:
+            assert (pl["tile_i"], pl["tile_j"], pl["warps"]) == (1, 1, 4)
+        s.sweep(T)
+        s.sync()
+        rho, t = s.get_state(0, 0)
+        tr = s.trace(0, 0)
+        assert t == T and np.isfinite(tr).all()
+        out.append((rho, tr, s.get_mu(0, 0)))
+        s.close()
+    for x, y in zip(out[0], out[1]):
+        np.testing.assert_array_equal(x, y)
