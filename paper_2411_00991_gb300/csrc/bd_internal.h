@@ -198,12 +198,15 @@ constexpr int kPropRing = 32;
 // not meet on the same L2 lines.
 constexpr int kProgStride = 32;
 __host__ __device__ inline SmemPlan smem_plan(int L, int f, int S, int n_tw, int n_ent, int max_nhalf, int tpi,
-                                              int tpj, int resident, int tsize, int teams, int stage = 0)
+                                              int tpj, int resident, int tsize, int teams, int stage = 0,
+                                              bool lean = false)
 {
     SmemPlan p;
     size_t o = 0;
     const int Le = L + f - 1, Lc = (Le - 1) / f + 1;
-    p.red = o; o += al16((size_t)2 * 8 * 8 * 4 * tsize);
+    // partial sums [prior, likelihood][8 sub-teams][8 warps][4]; two sets in
+    // two-team blocks of the lean form, whose later rounds alternate between them
+    p.red = o; o += al16((size_t)(lean && teams == 2 && !stage ? 2 : 1) * 2 * 8 * 8 * 4 * tsize);
     p.K = o; o += al16((size_t)Le * Le * tsize);
     p.tw = o; o += al16((size_t)2 * n_tw * tsize);
     p.ekl = o; o += al16((size_t)4 * n_ent);

@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
     const int rw = b_hi - b_lo;
 
     const SmemPlan sp = smem_plan(L, f, S, im.n_tw, im.n_ent, im.max_nhalf, ch.tpi, ch.tpj, RES ? 1 : 0, sizeof(T),
-                                  max(1, (int)blockDim.x / im.team), STG);
+                                  max(1, (int)blockDim.x / im.team), STG, LEAN);
     const StagePlan stp = stage_plan(L, im.max_nhalf, STG, RES ? 1 : 0);
     const int BW = stage_w(L);
     uint64_t* stg_bar = reinterpret_cast<uint64_t*>(smem + sp.stage_bar);   // [team][buffer]
@@ -557,13 +557,51 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
     };
     const int SR = S2 * rounds;   // rounds per sweep
     const bool ahead = SR > 1;
+    // In those team-barrier rounds of unstaged forms the second team barrier
+    // (after the decision) is dropped (nob2): the round's partial sums alternate
+    // between two buffers by round parity, so the next round's writes cannot
+    // meet this round's reads (a team reaches the next round's first barrier
+    // only when all its threads finished this round's decision), and proposals
+    // are drawn two rounds ahead, so a draw is published by the first barrier
+    // of the round before its own.  Needs more than two rounds per sweep (the
+    // draw two ahead must not be the current pixel's next update).
+    // (the lean form only: in the other forms the extra code costs more than
+    // the barrier -- measured)
+    const bool nob2 = LEAN && tb && SR > 2;
+    const int RB = 2 * 8 * 8 * 4;   // one set of partial sums
     const int pwarp = nwt > 1 ? 1 : 0;   // the drawing warp: not the one that polls the flags
     // one update per block and step (rounds == 1, n_sub == 1): a rejected
     // update scored on the neighbours' final state leaves nothing to write or
     // reread, so thread 0 publishes the step as soon as its wait ends
     // (s_pub: already published; thread 0 only)
+    // wide: with more than kPropRing rounds per sweep the warp's lanes draw
+    // several updates together, one each: the next kPropRing at every
+    // kPropRing-th round, or, two ahead (nob2), the next 16 at every 16th
     const bool wide = SR > kPropRing;
     auto draw_ahead = [&](int e0) {
+        const int e = e0 + (wide ? lane : 0);            // round ordinal of the draw
+        const int cs_e = e / rounds, r_e = e - cs_e * rounds;
+        const int q = r_e * n_sub + g;                   // this team's patch in that round
+        const int sw = cs_e / S2, cl = cs_e - sw * S2;
+        const int u1 = cl / S, v1 = cl - (cl / S) * S;
+        if (cs_e < ncs && q < npt) {
+            const int pi_ = pi0 + q / tw_, pj_ = pj0 + (q - (q / tw_) * tw_);
+            const Shape& sh1 = im.shape[shape_index(im, pi_, pj_)];
+            if (u1 < sh1.ph && v1 < sh1.pw) {
+                const int m1 = (pi_ * S + u1) * im.Wo + pj_ * S + v1;
+                T z1, lu1, rn1, dl1;
+                proposal<T>(im, ch, m1, t0 + 1 + sw, RES ? rho_s[(size_t)q * S2 + u1 * S + v1] : rho_g[m1], z1,
+                            lu1, rn1, dl1);
+                if (wide || lane == 0) {
+                    T* pe = ring + ((size_t)g * kPropRing + (e & (kPropRing - 1))) * 4;
+                    pe[0] = z1; pe[1] = lu1; pe[2] = rn1; pe[3] = dl1;
+                }
+            }
+        }
+    };
+    // (lean form: the first n lanes only, when wide)
+    auto draw_ahead_n = [&](int e0, int n) {
+        if (wide && lane >= n) return;
         const int e = e0 + (wide ? lane : 0);            // round ordinal of the draw
         const int cs_e = e / rounds, r_e = e - cs_e * rounds;
         const int q = r_e * n_sub + g;                   // this team's patch in that round
@@ -638,7 +676,18 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
             if ((stg_pend >> b) & 1u) stage_wait(b);
     };
     if (SANY) stage_issue(0);
-    if (ahead && in_team && twarp == pwarp) draw_ahead(0);
+    if (ahead && in_team && twarp == pwarp) {
+        if constexpr (LEAN) {
+            if (wide) {
+                draw_ahead_n(0, nob2 ? 18 : kPropRing);
+            } else {
+                draw_ahead_n(0, 1);
+                if (nob2) draw_ahead_n(1, 1);
+            }
+        } else {
+            draw_ahead(0);
+        }
+    }
     __syncthreads();
 
     for (int s = 0; s < nsteps; ++s) {
@@ -744,6 +793,15 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
             T phv[AUG ? NPX : 1];
             // staged window of this round (STG): buffer e & 1 of the team
             const int e_cur = cs * rounds + r, sb = e_cur & 1;
+            // this round's partial sums (alternating sets in nob2 rounds)
+            T* pr1 = red1;
+            T* pr2 = red2;
+            if constexpr (LEAN) {
+                if (nob2) {
+                    pr1 += (size_t)(e_cur & 1) * RB;
+                    pr2 += (size_t)(e_cur & 1) * RB;
+                }
+            }
             const float* wmu = reinterpret_cast<const float*>(stg_buf(sb) + stp.mu);
             const float4* wcum = reinterpret_cast<const float4*>(stg_buf(sb) + stp.cum);
             const float2* wcum2 = reinterpret_cast<const float2*>(stg_buf(sb) + stp.cum2);
@@ -788,10 +846,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
                 accA = warp_sum(accA);
                 const bool wb = __any_sync(0xffffffffu, badP);
                 if (lane == 0) {
-                    red1[twarp * 4 + 0] = accP;
-                    red1[twarp * 4 + 1] = accS;
-                    red1[twarp * 4 + 2] = accA;
-                    red1[twarp * 4 + 3] = wb ? (T)1 : (T)0;
+                    pr1[twarp * 4 + 0] = accP;
+                    pr1[twarp * 4 + 1] = accS;
+                    pr1[twarp * 4 + 2] = accA;
+                    pr1[twarp * 4 + 3] = wb ? (T)1 : (T)0;
                 }
             }
             // a3: likelihood change over the PSF window.  For the first round of
@@ -800,14 +858,14 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
             // accepted an update since this block last waited for it.
             if (active) {
                 if constexpr (AUG)
-                    lik_partial_aug<T, FINE, NPX>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4, lane,
+                    lik_partial_aug<T, FINE, NPX>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, pr2 + twarp * 4, lane,
                                              true);
                 else if constexpr (SWIN)
                     lik_partial_staged<RES>(wmu, wcum, wcum2, BW, wdx, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt,
-                                            NT, delta, red2 + twarp * 4, lane);
+                                            NT, delta, pr2 + twarp * 4, lane);
                 else
                     lik_partial<T, RES, CUM, FINE, NPX>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
-                                             delta, muv, red2 + twarp * 4, lane, cq, cq2, true);
+                                             delta, muv, pr2 + twarp * 4, lane, cq, cq2, true);
             }
             // a5: Metropolis-Hastings decision with the Hastings term of the log-space
             // walk, taken from the round's partial sums as soon as every warp of the
@@ -825,12 +883,12 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
                 bool bad = false;
                 dL = 0;
                 for (int w = 0; w < nwt; ++w) {
-                    sP += red1[w * 4 + 0];
-                    sS += red1[w * 4 + 1];
-                    sA += red1[w * 4 + 2];
-                    bad = bad || red1[w * 4 + 3] != (T)0;
-                    dL += red2[w * 4 + 0];
-                    bad = bad || red2[w * 4 + 1] != (T)0;
+                    sP += pr1[w * 4 + 0];
+                    sS += pr1[w * 4 + 1];
+                    sA += pr1[w * 4 + 2];
+                    bad = bad || pr1[w * 4 + 3] != (T)0;
+                    dL += pr2[w * 4 + 0];
+                    bad = bad || pr2[w * 4 + 1] != (T)0;
                 }
                 dP = sP + (T)(sh.K - 1) * P::log1p(sS / sA);
                 const T tot = dL + dP;
@@ -842,7 +900,13 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
             // need not wait for it there; it overlaps the neighbour wait below
             if (ahead && in_team && twarp == pwarp) {
                 const int e = cs * rounds + r;
-                if (!wide || (e & (kPropRing - 1)) == kPropRing - 1) draw_ahead(e + 1);
+                if constexpr (LEAN) {
+                    if (!wide) draw_ahead_n(e + (nob2 ? 2 : 1), 1);
+                    else if (nob2) { if ((e & 15) == 0 && e > 0) draw_ahead_n(e + 2, 16); }
+                    else if ((e & (kPropRing - 1)) == kPropRing - 1) draw_ahead_n(e + 1, kPropRing);
+                } else {
+                    if (!wide || (e & (kPropRing - 1)) == kPropRing - 1) draw_ahead(e + 1);
+                }
             }
             if (r == 0 && s > 0 && tid < 32) {
                 // stale: a neighbour changed data this window reads at its step s-1
@@ -883,7 +947,11 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
             } else if (blk) {
                 any_accept = __syncthreads_or(active && accept ? 1 : 0);
             } else {
-                tsync();
+                if constexpr (LEAN) {
+                    if (!nob2) tsync();
+                } else {
+                    tsync();
+                }
                 any_accept = active && accept ? 1 : 0;
             }
             if (blk && s_abort) {
@@ -894,7 +962,7 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
             if (stale) {
                 if (active) {
                     if constexpr (AUG) {
-                        lik_partial_aug<T, FINE, NPX>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, red2 + twarp * 4,
+                        lik_partial_aug<T, FINE, NPX>(mu_g, phi_g, Ks, im, i, j, lt, NT, delta, muv, phv, pr2 + twarp * 4,
                                                  lane, false);
                     } else if constexpr (SWIN) {
                         // the speculative copy is stale: copy the window again (every
@@ -902,10 +970,10 @@ __global__ void __launch_bounds__(256, std::is_same<T, float>::value ? (LEAN ? 4
                         stage_issue(e_cur);
                         stage_wait(sb);
                         lik_partial_staged<RES>(wmu, wcum, wcum2, BW, wdx, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw,
-                                                lt, NT, delta, red2 + twarp * 4, lane);
+                                                lt, NT, delta, pr2 + twarp * 4, lane);
                     } else {
                         lik_partial<T, RES, CUM, FINE, NPX>(mu_g, cum_g, cum2_g, dat_s, dat_g, Ks, im, i, j, a_lo, b_lo, rw, lt, NT,
-                                                 delta, muv, red2 + twarp * 4, lane, cq, cq2, false);
+                                                 delta, muv, pr2 + twarp * 4, lane, cq, cq2, false);
                     }
                 }
                 __syncthreads();

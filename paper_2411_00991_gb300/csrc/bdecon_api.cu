@@ -322,14 +322,15 @@ int item_blocks(const PlanItem& it)
     return (int)it.chains.size() * ((it.ph->npi + it.tpi - 1) / it.tpi) * ((it.ph->npj + it.tpj - 1) / it.tpj);
 }
 
-size_t items_smem(const std::vector<PlanItem*>& items, int resident, int ts, int threads, int stage)
+size_t items_smem(const std::vector<PlanItem*>& items, int resident, int ts, int threads, int stage,
+                  bool lean = false)
 {
     size_t mx = 0;
     for (const PlanItem* it : items) {
         const ProbHost& ph = *it->ph;
         const int teams = std::max(1, threads / it->team);   // update teams per block
         const SmemPlan sp = smem_plan(ph.L, ph.f, ph.S, ph.n_tw, (int)ph.ent_kl.size(), ph.max_nhalf, it->tpi,
-                                      it->tpj, resident, ts, teams, stage);
+                                      it->tpj, resident, ts, teams, stage, lean);
         mx = std::max(mx, sp.total);
     }
     return mx;
@@ -396,7 +397,7 @@ bool plan_items(int precision, int sms, std::vector<PlanItem*>& items, Group& g,
             for (PlanItem* it : items)
                 if (!it->user) it->tpi = it->tpj = 1;
             for (;;) {
-                const size_t smem = items_smem(items, resident, ts, g.threads, stage);
+                const size_t smem = items_smem(items, resident, ts, g.threads, stage, want_lean && stage == 0);
                 int tot = 0;
                 for (const PlanItem* it : items) tot += item_blocks(*it);
                 if (smem <= kMaxSmem) {
