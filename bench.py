@@ -649,7 +649,8 @@ def run_reference(args):
 def run_profile(args):
     """Small cases for ncu: --profile N runs one launch of N sweeps of the
     512x512 frame after a warm-up launch; --profile-batch L runs two sweeps of
-    the batch frames whose PSF side is L (one launch group)."""
+    the batch frames whose PSF side is L (one launch group); --profile-lowsnr
+    runs two one-sweep launches of the 2048x2048 low-SNR frame (4 chains)."""
     import torch
     from paper_2411_00991_gb300 import bdecon as bd
     st = torch.cuda.current_stream().cuda_stream
@@ -665,6 +666,18 @@ def run_profile(args):
         s.sync()
         print(json.dumps({"profile_batch_L": args.profile_batch, "images": len(probs), "sides": [q.H for q in probs],
                           "updates_per_sweep": obj_updates(probs), "plan": s.get_plan()}))
+        s.close()
+        return
+    if args.profile_lowsnr:
+        prob = synth.lowsnr_2048()
+        prob.truth = None
+        s = bd.Sampler(prob, precision=bd.BDECON_FP32, max_sweeps=16, stream=st)
+        s.sweep(1)
+        s.sync()
+        s.sweep(1)
+        s.sync()
+        print(json.dumps({"profile_lowsnr": True, "updates_per_sweep": obj_updates([prob]), "plan": s.get_plan(),
+                          "lean": s.lean()}))
         s.close()
         return
     prob = synth.widefield_512()
@@ -694,8 +707,9 @@ def main():
     ap.add_argument("--profile", type=int, default=0, help="ncu mode: one launch of this many sweeps")
     ap.add_argument("--profile-fp64", action="store_true")
     ap.add_argument("--profile-batch", type=int, default=0, help="ncu mode: the batch frames of this PSF side")
+    ap.add_argument("--profile-lowsnr", action="store_true", help="ncu mode: the 2048x2048 low-SNR frame")
     args = ap.parse_args()
-    if args.profile or args.profile_batch:
+    if args.profile or args.profile_batch or args.profile_lowsnr:
         run_profile(args)
         return
     if args.warmup < 3:
